@@ -1,0 +1,396 @@
+#!/usr/bin/env python3
+"""Benchmark of the BOAC hot path: batched Bayesian-optimisation candidate
+evaluation (rasterise mu -> 50 MLEM iterations -> Poisson score) at 128x128
+pixels, 120 views, 128 bins, 256 candidates per GPU.
+
+One step = the whole hot path for one batch: boac_rasterize_mu (Eq. 3-4) and
+boac_mlem (sensitivity, 50 fused MLEM iterations, Eq. 5 score) for all 256
+candidates.  Metric: candidate-iterations per second (256 * 50 per step).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+(the only reference this paper has: it publishes no code) on the host cores.
+Multi-GPU (torchrun): every rank evaluates its own 256 candidates (weak
+scaling, no collective on the data path); the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2109_11920_gb300 import synth  # noqa: E402
+
+WL = synth.BATCHED
+METRIC = "MLEM candidate-iterations/sec at 128x128x120 views and % HBM roofline vs plain GPU path"
+UNIT = "candidate-iterations/s"
+CONFIG = {
+    "workload": f"{WL.name}: {WL.B} BO candidates x {WL.K} MLEM iterations, "
+                f"{WL.n}x{WL.n} px of {WL.dx} cm, {WL.V} views over 360 deg, {WL.n} bins, "
+                f"{WL.counts:.0e} counts, shared sinogram",
+    "candidates_per_gpu": WL.B,
+    "iterations": WL.K,
+    "image": WL.n,
+    "views": WL.V,
+    "bins": WL.n,
+    "l2": "flushed (256 MiB write) before every timed step; per-step CUDA events summed",
+}
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+PROFILE_FILE = os.path.join(ROOT, "profiles", "mlem_fused_bo_batch128_v120.md")
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ----------------------------------------------------------------- inputs
+def make_inputs_gpu(dev, boac, Geom, Tissue, seed=0):
+    """Synthetic workload built on the device: true head (Legendre c_true) ->
+    rasterised mu -> phantom (brain 1.0, four ellipses 4.0) -> projected,
+    scaled to the count level, Poisson noise -> 256 perturbed candidates."""
+    import torch
+    g = Geom.make(WL.n, WL.dx, WL.V)
+    t = Tissue(*synth.TISSUE)
+    ph, noise, cand = synth.streams(seed)
+    c_true = torch.tensor([synth.C_TRUE], dtype=torch.float32, device=dev)
+    mu_true = boac.boac_rasterize_mu(g, t, c_true)
+    brain = (mu_true[0] == np.float32(synth.TISSUE[0])).cpu().numpy()
+    F_true = synth.paint_activity(WL.n, float(np.float32(WL.dx)), brain, synth.ellipses(ph, synth.C_TRUE[0]))
+    q = boac.boac_project(g, mu_true, torch.tensor(F_true[None], dtype=torch.float32, device=dev))
+    S = synth.poisson_sinogram(noise, q[0].double().cpu().numpy(), WL.counts)
+    coefs = synth.candidates(cand, WL.B).astype(np.float32)
+    return g, t, coefs, S.astype(np.float32)
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- helpers
+def measured_peak_gbs():
+    try:
+        with open(PEAKS_FILE) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def fused_source_hash():
+    h = hashlib.sha256()
+    for f in ("boac_fused.cu", "boac_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2109_11920_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the fused kernel from the committed ncu summary,
+    if it was taken on the current kernel source (else None)."""
+    try:
+        text = open(PROFILE_FILE).read()
+    except OSError:
+        return None
+    m_src = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]{16})", text)
+    m_b = re.search(r"dram_bytes_per_launch_full_size:\s*([0-9.eE+]+)", text)
+    if not m_src or not m_b or m_src.group(1) != fused_source_hash():
+        return None
+    return float(m_b.group(1))
+
+
+def algorithmic_bytes_per_cand_iter(n, V):
+    """Per candidate-iteration: the attenuation table read in the forward and
+    in the backward pass (2 x 4 V n^2 bytes), plus F read+write, sens read
+    (3 x 4 n^2) and the sinogram (4 V n)."""
+    return 8.0 * V * n * n + 4.0 * (3 * n * n + V * n)
+
+
+# ----------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    import oracle
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    K_ref = 20
+    import sys as _s
+    _s.path.insert(0, os.path.join(ROOT, "tests"))
+    from problems import make_problem
+    p = make_problem(WL.n, WL.dx, WL.V, WL.counts, B=cores, seed=WL.seed)
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        _, _, used = oracle.mlem_batch(p.geom, p.mu, p.S, K_ref, with_score=True, nthreads=cores)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    tot = sum(times)
+    value = cores * K_ref * len(times) / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": CONFIG,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle",
+                         "sample": f"per step {cores} candidates x {K_ref} MLEM iterations + score "
+                                   f"of the {WL.n}x{WL.n}/{WL.V}-view batch, one candidate per thread"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline_sample():
+    """The oracle as it stands, timed on this host's cores (bounded sample)."""
+    import oracle
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from problems import make_problem
+    cores = os.cpu_count() or 1
+    K = WL.K
+    B = 4 * cores
+    p = make_problem(WL.n, WL.dx, WL.V, WL.counts, B=B, seed=WL.seed)
+    t0 = time.perf_counter()
+    _, _, used = oracle.mlem_batch(p.geom, p.mu, p.S, K, with_score=True, nthreads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": B * K / dt, "unit": UNIT, "cores": used, "kind": "oracle",
+            "sample": f"{B} candidates x {K} MLEM iterations + score of the "
+                      f"{WL.n}x{WL.n}/{WL.V}-view batch (FP64 C, candidates spread over "
+                      f"{used} threads), {dt:.1f} s wall"}
+
+
+# ----------------------------------------------------------------- GPU arm
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    from paper_2109_11920_gb300 import Geom, Tissue
+    from paper_2109_11920_gb300 import api as boac
+    from paper_2109_11920_gb300 import build as pkg_build
+
+    pkg_build.build()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    g, t, coefs, S_np = make_inputs_gpu(dev, boac, Geom, Tissue, seed=WL.seed + rank)
+    B, K = WL.B, WL.K
+    c_d = torch.tensor(coefs, device=dev)
+    S_d = torch.tensor(S_np, device=dev)
+    mu = torch.empty(B, WL.n, WL.n, device=dev)
+    F = torch.empty(B, WL.n, WL.n, device=dev)
+    L = torch.empty(B, dtype=torch.float64, device=dev)
+    ws = boac.workspace(g, B, boac._lib.OP_MLEM, dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(ev_k=None):
+        boac.boac_rasterize_mu(g, t, c_d, out=mu)
+        F.fill_(1.0)
+        if ev_k is not None:
+            ev_k[0].record(stream)
+        boac.boac_mlem(g, mu, S_d, F, K, score=True, ws=ws, L=L)
+        if ev_k is not None:
+            ev_k[1].record(stream)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+
+    E = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    ev = [(E(), E()) for _ in range(args.steps)]
+    evk = [(E(), E()) for _ in range(args.steps)]
+    barrier()
+    with ClockSampler(local_rank) as clk:
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            ev[i][0].record(stream)
+            step(evk[i])
+            ev[i][1].record(stream)
+        torch.cuda.synchronize(dev)
+    barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    kern_ms = [a.elapsed_time(b) for a, b in evk]
+    tot_ms = sum(step_ms)
+    if world > 1:
+        tt = torch.tensor([tot_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        tot_ms = float(tt.item())
+    value = world * B * K * args.steps / (tot_ms / 1e3)
+    assert torch.isfinite(L).all(), "non-finite score"
+
+    # ---- end to end through the public API with host buffers (pinned)
+    c_h = torch.tensor(coefs).pin_memory()
+    S_h = torch.tensor(S_np).pin_memory()
+    L_h = torch.empty(B, dtype=torch.float64).pin_memory()
+    F_h = torch.empty(B, WL.n, WL.n).pin_memory()
+
+    def e2e_step():
+        c_d.copy_(c_h, non_blocking=True)
+        S_d.copy_(S_h, non_blocking=True)
+        step()
+        L_h.copy_(L, non_blocking=True)
+        F_h.copy_(F, non_blocking=True)
+
+    for _ in range(max(1, args.warmup // 2)):
+        e2e_step()
+    torch.cuda.synchronize(dev)
+    e_ms = []
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        a, b = E(), E()
+        a.record(stream)
+        e2e_step()
+        b.record(stream)
+        b.synchronize()
+        e_ms.append(a.elapsed_time(b))
+    e_tot = sum(e_ms)
+    if world > 1:
+        tt = torch.tensor([e_tot], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e_tot = float(tt.item())
+    e2e = {"value": world * B * K * args.steps / (e_tot / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": c_h.numel() * 4 + S_h.numel() * 4,
+           "d2h_bytes_per_step": L_h.numel() * 8 + F_h.numel() * 4}
+
+    if rank != 0:
+        return
+
+    # ---- plain launch-per-step path (one candidate at a time), sampled
+    nplain = 4
+    Fp = torch.ones(nplain, WL.n, WL.n, device=dev)
+    wsp = boac.workspace(g, nplain, boac._lib.OP_MLEM_PLAIN, dev)
+    boac.boac_mlem(g, mu[:nplain].contiguous(), S_d, Fp, 2, plain=True, ws=wsp)
+    torch.cuda.synchronize(dev)
+    a, b = E(), E()
+    Fp.fill_(1.0)
+    a.record(stream)
+    boac.boac_mlem(g, mu[:nplain].contiguous(), S_d, Fp, K, plain=True, ws=wsp)
+    b.record(stream)
+    b.synchronize()
+    plain_value = nplain * K / (a.elapsed_time(b) / 1e3)
+
+    # ---- roofline of the dominant kernel (the fused MLEM kernel)
+    kavg_s = sum(kern_ms) / len(kern_ms) / 1e3
+    alg = algorithmic_bytes_per_cand_iter(WL.n, WL.V) * B * K
+    peak, peak_kind = measured_peak_gbs()
+    achieved = alg / kavg_s / 1e9
+    traffic = profiled_traffic()
+    roof = {"bound": "hbm", "kernel": "mlem_fused_kernel<128,1024>", "achieved": achieved,
+            "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+            "peak_kind": f"{peak_kind} hbm_gbs (copy)",
+            "algorithmic_bytes_per_launch": alg,
+            "kernel_ms": 1e3 * kavg_s}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": dict(CONFIG, global_batch=world * B, parallelism=f"replicas{world}"),
+        "roofline": roof,
+        "e2e": e2e,
+        "gpu_launches": 2 * args.steps,
+        "clocks": clk.summary(),
+        "plain_path": {"value": plain_value, "unit": UNIT, "sample": f"{nplain} candidates x {K} iterations",
+                       "speedup_of_batched": value / world / plain_value},
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_sample()
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    try:
+        run_gpu(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,171 @@
+/*
+ * boac.h -- C ABI of the BOAC hot path on GB300 (sm_103a).
+ *
+ * Method: Koutsantonis et al., "A Bayesian Optimization Approach for
+ * Attenuation Correction in SPECT Brain Imaging" (arXiv 2109.11920).  For
+ * every candidate head geometry c_0..c_5 proposed by the Bayesian optimiser
+ * the library rasterises the attenuation map (Eq. 3-4), applies the
+ * attenuated Radon transform S = A^mu F (Eq. 1-2) and its exact adjoint,
+ * runs a fixed number of MLEM iterations (Sec. III, step 3) and scores the
+ * candidate with the Poisson log-likelihood (Eq. 5).
+ *
+ * Discretisation (the paper gives none; both this library and its test
+ * oracle use this one):
+ *   - image: n x n pixels of pixel_cm; pixel (i, j) (row i, column j) has its
+ *     centre at x = (j - c) pixel_cm, y = (i - c) pixel_cm, c = (n - 1) / 2;
+ *   - views: phi_v = 2 pi v / n_views, v = 0 .. n_views - 1;
+ *   - detector: n_bins = n bins of bin_cm = pixel_cm, bin b at s = (b - c) bin_cm;
+ *   - ray: n samples one pixel apart, sample k at t = (k - c) pixel_cm along
+ *     (-sin phi, cos phi); the detector lies at t -> +infinity;
+ *   - F and mu are sampled bilinearly at the ray samples (0 outside the grid);
+ *   - attenuation of sample k: a = exp(-pixel_cm (mu_k / 2 + sum_{k' > k} mu_k'));
+ *   - q(v, b) = pixel_cm * sum_k a_k F_k.
+ *
+ * Conventions for every entry point:
+ *   - All array arguments are DEVICE pointers to caller-owned, contiguous,
+ *     row-major float32 (or float64 where stated) memory on the current CUDA
+ *     device.  The library allocates no device memory: operations that need
+ *     scratch take a caller-allocated workspace (see boac_workspace_bytes).
+ *   - Work is enqueued asynchronously on `stream` (a cudaStream_t; NULL =
+ *     the legacy default stream).  Return values report argument and launch
+ *     errors only; kernel faults surface at the next synchronisation.
+ *   - Return BOAC_OK (0) on success or a negative BOAC_E* status.  Nothing is
+ *     enqueued when an argument check fails.
+ *   - Geometry restrictions: 8 <= n <= 256 with n_bins == n and
+ *     bin_cm == pixel_cm; 2 <= n_views <= 720 and n_views even for the
+ *     fused path (boac_mlem, boac_score_grad).
+ */
+#ifndef BOAC_H
+#define BOAC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define BOAC_OK 0
+#define BOAC_EINVAL (-1)       /* bad shape, null pointer, stride or mode   */
+#define BOAC_ECUDA (-2)        /* a CUDA call or launch failed              */
+#define BOAC_EWORKSPACE (-3)   /* workspace missing or too small            */
+#define BOAC_EUNSUPPORTED (-4) /* valid geometry this build has no kernel for */
+
+/* ---- types ------------------------------------------------------------- */
+/* Scanner geometry (see the discretisation above). */
+typedef struct {
+    int n;          /* image side in pixels (also the ray sample count)    */
+    int n_bins;     /* detector bins per view; must equal n                */
+    int n_views;    /* views uniformly spaced over 360 degrees             */
+    float pixel_cm; /* pixel size in cm                                    */
+    float bin_cm;   /* bin pitch in cm; must equal pixel_cm                */
+} boac_geom;
+
+/* Tissue values of the model attenuation map (Eq. 4): brain mu_b and
+ * cranium mu_c in cm^-1, cranium thickness dR in cm.  Fixed, not optimised
+ * (Sec. II). */
+typedef struct {
+    float mu_b, mu_c, dR;
+} boac_tissue;
+
+enum { BOAC_RASTER_CENTER = 0, BOAC_RASTER_AREA = 1 };
+
+/* Workspace queries: which operation the size is for. */
+enum {
+    BOAC_OP_PROJECT = 0,
+    BOAC_OP_BACKPROJECT = 1,
+    BOAC_OP_MLEM = 2,
+    BOAC_OP_MLEM_PLAIN = 3,
+    BOAC_OP_SCORE = 4,
+    BOAC_OP_SCORE_GRAD = 5
+};
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char *boac_status_string(int status);
+
+/* ABI version of this library (incremented on incompatible changes). */
+int boac_abi_version(void);
+
+/* Bytes of device workspace that `op` needs for B candidates of geometry g
+ * on the current device (0 if none).  For BOAC_OP_SCORE_GRAD the size also
+ * depends on K and ckpt_every: use boac_score_grad_workspace_bytes.
+ * Returns 0 and sets nothing on invalid arguments. */
+size_t boac_workspace_bytes(const boac_geom *g, int B, int op);
+
+/* ---- Eq. 3-4: model attenuation map ------------------------------------
+ * R(theta) = max(0, sum_{k=0..5} c_k P_k(cos theta)), theta = atan2(y, x)
+ * (Eq. 3; P_k Legendre polynomials), then Eq. 4 at every pixel centre:
+ *   CENTER: mu_b where r < R, mu_c where R <= r < R + dR, 0 beyond;
+ *   AREA:   mu_b f(R) + mu_c (f(R + dR) - f(R)),
+ *           f(R') = clamp(1/2 + (R' - r) / pixel_cm, 0, 1)
+ *           (one-pixel radial ramp; differentiable in c).
+ * Computed in float64, stored as float32.
+ *   c   [B][6]     Legendre coefficients in cm (device, float32)
+ *   mu  [B][n][n]  output, cm^-1 (device, float32)
+ * Errors: BOAC_EINVAL for null pointers, B < 1, bad mode or geometry. */
+int boac_rasterize_mu(const boac_geom *g, const boac_tissue *t, const float *c,
+                      int B, int mode, float *mu, void *stream);
+
+/* ---- Eq. 1-2: forward projection q = A^mu F ----------------------------
+ *   mu  [B][n][n], F [B][n][n]   (device, float32)
+ *   q   [B][n_views][n_bins]     output (device, float32)
+ * The attenuation is integrated along each ray on the fly; no workspace. */
+int boac_project(const boac_geom *g, const float *mu, const float *F, int B,
+                 float *q, void *stream);
+
+/* ---- Eq. 2 adjoint: out = (A^mu)^T y -----------------------------------
+ * Exact transpose of boac_project (same bilinear weights), computed as a
+ * gather so that the result is deterministic.
+ *   y   [B][n_views][n_bins] (device, float32); NULL means y = 1 everywhere
+ *       (the MLEM sensitivity image)
+ *   out [B][n][n]            output (device, float32)
+ *   ws  workspace of boac_workspace_bytes(g, B, BOAC_OP_BACKPROJECT) bytes
+ *       (holds the attenuation factors of every ray sample). */
+int boac_backproject(const boac_geom *g, const float *mu, const float *y,
+                     int B, float *out, void *ws, size_t ws_bytes,
+                     void *stream);
+
+/* ---- MLEM (Sec. III step 3; Shepp & Vardi) ------------------------------
+ * For each candidate b: sens = A^T 1, then K times
+ *   q = A F;  r = S / q (0 where q <= 0);  F <- F * (A^T r) / sens
+ * (0 where sens == 0).  Optionally scores the result with Eq. 5:
+ *   L[b] = sum_i S_i ln q_i - q_i [- ln S_i!]   at q = A F^K,
+ * reduced in float64 (0 ln q := 0 where S_i = 0; -inf where q_i = 0 < S_i).
+ *   mu       [B][n][n]                         (device, float32)
+ *   S        measured sinogram(s), [n_views][n_bins] per candidate,
+ *            candidate b's at S + b * s_stride floats; s_stride = 0 shares
+ *            one sinogram between all candidates
+ *   F        [B][n][n] in: initial image (e.g. ones), out: F^K
+ *   K        iterations (>= 0)
+ *   L        [B] float64 output, or NULL to skip the score
+ * boac_mlem is the batched path: one persistent fused kernel runs every
+ * iteration of every candidate on chip.  boac_mlem_plain is the
+ * launch-per-step path: one candidate at a time, separate project / ratio /
+ * backproject / update kernels per iteration (the comparison baseline).
+ * Workspace: boac_workspace_bytes(g, B, BOAC_OP_MLEM / BOAC_OP_MLEM_PLAIN). */
+int boac_mlem(const boac_geom *g, const float *mu, const float *S,
+              long long s_stride, float *F, int K, int B, double *L,
+              int include_lgamma, void *ws, size_t ws_bytes, void *stream);
+int boac_mlem_plain(const boac_geom *g, const float *mu, const float *S,
+                    long long s_stride, float *F, int K, int B, double *L,
+                    int include_lgamma, void *ws, size_t ws_bytes,
+                    void *stream);
+
+/* ---- Eq. 5: score of given images ---------------------------------------
+ * L[b] = sum_i S_i ln q_i - q_i [- ln S_i!], q = A^mu F (float32 projection,
+ * float64 reduction; same conventions as boac_mlem).
+ *   ws  boac_workspace_bytes(g, B, BOAC_OP_SCORE) bytes (holds q). */
+int boac_score(const boac_geom *g, const float *mu, const float *S,
+               long long s_stride, const float *F, int B, int include_lgamma,
+               double *L, void *ws, size_t ws_bytes, void *stream);
+
+/* Eq. 5 reduction alone, for expected counts q already on the device:
+ *   q [B][n_views][n_bins] float32, S as above, L [B] float64 output. */
+int boac_loglik(const boac_geom *g, const float *q, const float *S,
+                long long s_stride, int B, int include_lgamma, double *L,
+                void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BOAC_H */

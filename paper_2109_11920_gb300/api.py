@@ -1,0 +1,161 @@
+"""Torch-facing wrappers of the C ABI, one per entry point, same names.
+
+Each function checks that its tensors are contiguous CUDA tensors of the
+right dtype and shape, allocates outputs and the workspace the library asks
+for with torch, and calls the C entry point on the current stream.  Nothing
+here computes any part of the method.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib
+from ._lib import Geom, Tissue, check
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(device) -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _need(t: torch.Tensor, name: str, dtype, shape=None):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor (the library has no CPU path)")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return t
+
+
+def _sino(S: torch.Tensor, g: Geom, B: int):
+    """Shared [V, nb] or per-candidate [B, V, nb] sinogram -> (tensor, stride)."""
+    _need(S, "S", torch.float32)
+    if tuple(S.shape) == (g.n_views, g.n_bins):
+        return S, 0
+    if tuple(S.shape) == (B, g.n_views, g.n_bins):
+        return S, g.n_views * g.n_bins
+    raise ValueError(f"S must be [{g.n_views}, {g.n_bins}] or [{B}, {g.n_views}, {g.n_bins}]")
+
+
+def boac_workspace_bytes(g: Geom, B: int, op: int) -> int:
+    return int(_lib.load().boac_workspace_bytes(ctypes.byref(g), int(B), int(op)))
+
+
+def workspace(g: Geom, B: int, op: int, device) -> torch.Tensor | None:
+    nbytes = boac_workspace_bytes(g, B, op)
+    if nbytes == 0:
+        return None
+    return torch.empty(nbytes, dtype=torch.uint8, device=device)
+
+
+def boac_rasterize_mu(g: Geom, t: Tissue, c: torch.Tensor, mode: int = _lib.RASTER_CENTER,
+                      out: torch.Tensor | None = None) -> torch.Tensor:
+    """Eq. 3-4: mu[B, n, n] (cm^-1) from Legendre coefficients c[B, 6] (cm)."""
+    _need(c, "c", torch.float32)
+    if c.dim() != 2 or c.shape[1] != 6:
+        raise ValueError("c must be [B, 6]")
+    B = c.shape[0]
+    mu = out if out is not None else torch.empty(B, g.n, g.n, dtype=torch.float32, device=c.device)
+    _need(mu, "mu", torch.float32, (B, g.n, g.n))
+    check("boac_rasterize_mu", _lib.load().boac_rasterize_mu(
+        ctypes.byref(g), ctypes.byref(t), _ptr(c), B, int(mode), _ptr(mu), _stream(c.device)))
+    return mu
+
+
+def boac_project(g: Geom, mu: torch.Tensor, F: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+    """Eq. 1-2: q[B, V, nb] = A^mu F."""
+    _need(mu, "mu", torch.float32)
+    B = mu.shape[0]
+    _need(mu, "mu", torch.float32, (B, g.n, g.n))
+    _need(F, "F", torch.float32, (B, g.n, g.n))
+    q = out if out is not None else torch.empty(B, g.n_views, g.n_bins, dtype=torch.float32, device=mu.device)
+    _need(q, "q", torch.float32, (B, g.n_views, g.n_bins))
+    check("boac_project", _lib.load().boac_project(
+        ctypes.byref(g), _ptr(mu), _ptr(F), B, _ptr(q), _stream(mu.device)))
+    return q
+
+
+def boac_backproject(g: Geom, mu: torch.Tensor, y: torch.Tensor | None,
+                     out: torch.Tensor | None = None, ws: torch.Tensor | None = None) -> torch.Tensor:
+    """Adjoint of Eq. 2: out[B, n, n] = (A^mu)^T y (y=None: the sensitivity A^T 1)."""
+    _need(mu, "mu", torch.float32)
+    B = mu.shape[0]
+    _need(mu, "mu", torch.float32, (B, g.n, g.n))
+    if y is not None:
+        _need(y, "y", torch.float32, (B, g.n_views, g.n_bins))
+    res = out if out is not None else torch.empty(B, g.n, g.n, dtype=torch.float32, device=mu.device)
+    _need(res, "out", torch.float32, (B, g.n, g.n))
+    if ws is None:
+        ws = workspace(g, B, _lib.OP_BACKPROJECT, mu.device)
+    check("boac_backproject", _lib.load().boac_backproject(
+        ctypes.byref(g), _ptr(mu), _ptr(y), B, _ptr(res), _ptr(ws), ws.numel(), _stream(mu.device)))
+    return res
+
+
+def boac_mlem(g: Geom, mu: torch.Tensor, S: torch.Tensor, F: torch.Tensor, K: int,
+              score: bool = True, include_lgamma: bool = True, plain: bool = False,
+              ws: torch.Tensor | None = None, L: torch.Tensor | None = None):
+    """K MLEM iterations in place on F[B, n, n]; returns (F, L[B] float64 or None).
+
+    ``plain=False`` runs the batched persistent fused kernel; ``plain=True``
+    the launch-per-step baseline (one candidate at a time)."""
+    _need(mu, "mu", torch.float32)
+    B = mu.shape[0]
+    _need(mu, "mu", torch.float32, (B, g.n, g.n))
+    _need(F, "F", torch.float32, (B, g.n, g.n))
+    S, stride = _sino(S, g, B)
+    op = _lib.OP_MLEM_PLAIN if plain else _lib.OP_MLEM
+    if ws is None:
+        ws = workspace(g, B, op, mu.device)
+    if score and L is None:
+        L = torch.empty(B, dtype=torch.float64, device=mu.device)
+    if L is not None:
+        _need(L, "L", torch.float64, (B,))
+    fn = _lib.load().boac_mlem_plain if plain else _lib.load().boac_mlem
+    check("boac_mlem_plain" if plain else "boac_mlem",
+          fn(ctypes.byref(g), _ptr(mu), _ptr(S), stride, _ptr(F), int(K), B,
+             _ptr(L) if score else None, int(include_lgamma), _ptr(ws),
+             ws.numel() if ws is not None else 0, _stream(mu.device)))
+    return F, (L if score else None)
+
+
+def boac_mlem_plain(g, mu, S, F, K, score=True, include_lgamma=True, ws=None, L=None):
+    return boac_mlem(g, mu, S, F, K, score=score, include_lgamma=include_lgamma, plain=True, ws=ws, L=L)
+
+
+def boac_score(g: Geom, mu: torch.Tensor, S: torch.Tensor, F: torch.Tensor,
+               include_lgamma: bool = True, ws: torch.Tensor | None = None) -> torch.Tensor:
+    """Eq. 5 at q = A^mu F: L[B] float64."""
+    _need(mu, "mu", torch.float32)
+    B = mu.shape[0]
+    _need(F, "F", torch.float32, (B, g.n, g.n))
+    S, stride = _sino(S, g, B)
+    if ws is None:
+        ws = workspace(g, B, _lib.OP_SCORE, mu.device)
+    L = torch.empty(B, dtype=torch.float64, device=mu.device)
+    check("boac_score", _lib.load().boac_score(
+        ctypes.byref(g), _ptr(mu), _ptr(S), stride, _ptr(F), B, int(include_lgamma), _ptr(L),
+        _ptr(ws), ws.numel(), _stream(mu.device)))
+    return L
+
+
+def boac_loglik(g: Geom, q: torch.Tensor, S: torch.Tensor, include_lgamma: bool = True) -> torch.Tensor:
+    """Eq. 5 reduction of given expected counts q[B, V, nb]: L[B] float64."""
+    _need(q, "q", torch.float32)
+    B = q.shape[0]
+    _need(q, "q", torch.float32, (B, g.n_views, g.n_bins))
+    S, stride = _sino(S, g, B)
+    L = torch.empty(B, dtype=torch.float64, device=q.device)
+    check("boac_loglik", _lib.load().boac_loglik(
+        ctypes.byref(g), _ptr(q), _ptr(S), stride, B, int(include_lgamma), _ptr(L), _stream(q.device)))
+    return L

@@ -1,0 +1,115 @@
+// boac_device.cuh -- device helpers shared by every kernel of the library:
+// view angles, ray-sample coordinates, bilinear sampling and its transpose.
+//
+// Every kernel computes the continuous pixel coordinates (u, w) of ray sample
+// (k, b) with sample_uw(), so the forward projector, the back-projector and
+// the gradient all use bit-identical bilinear weights (the back-projector is
+// the exact transpose of the projector in float32 up to summation order).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/boac.h"
+
+namespace boac {
+
+// cos/sin of phi_v = 2 pi v / V (Sec. V: views uniformly spaced over the full
+// angular range).  The quadrant is taken exactly, so views a quarter turn
+// apart are exact rotations of each other; the in-quadrant angle is
+// evaluated in float64 and rounded once to float32.
+__device__ __forceinline__ void view_cos_sin(int v, int V, float* cs, float* sn) {
+    long long four_v = 4LL * (long long)v;
+    int quadrant = (int)((four_v / V) % 4);
+    long long rem = four_v % V;
+    double th = 1.5707963267948966192 * (double)rem / (double)V;
+    double s, c;
+    sincos(th, &s, &c);
+    float fc = (float)c, fs = (float)s;
+    switch (quadrant) {
+        case 0: *cs = fc; *sn = fs; break;
+        case 1: *cs = -fs; *sn = fc; break;
+        case 2: *cs = -fc; *sn = -fs; break;
+        default: *cs = fs; *sn = -fc; break;
+    }
+}
+
+// Continuous (column u, row w) pixel index of ray sample k of bin b in the
+// view with (cs, sn): p = s (cs, sn) + t (-sn, cs), s = (b - c) dx,
+// t = (k - c) dx, c = (n - 1) / 2 (bins and samples share the pixel pitch).
+__device__ __forceinline__ void sample_uw(int k, int b, float cs, float sn, float c,
+                                          float* u, float* w) {
+    float bc = (float)b - c;
+    float kc = (float)k - c;
+    *u = fmaf(bc, cs, fmaf(-kc, sn, c));
+    *w = fmaf(bc, sn, fmaf(kc, cs, c));
+}
+
+__device__ __forceinline__ bool inside_open(float u, float w, int n) {
+    return u > -1.0f && u < (float)n && w > -1.0f && w < (float)n;
+}
+
+// Bilinear sample of a zero-padded shared-memory image.  `img` points at
+// padded element (0, 0) = pixel (-1, -1); rows are P floats apart; the pad
+// ring (pixels -1 and n) holds zeros.  Samples outside (-1, n)^2 are 0.
+__device__ __forceinline__ float bilerp_padded(const float* img, int P, int n, float u, float w) {
+    if (!inside_open(u, w, n)) return 0.0f;
+    float fj = floorf(u), fi = floorf(w);
+    float au = u - fj, aw = w - fi;
+    const float* p = img + ((int)fi + 1) * P + ((int)fj + 1);
+    float v00 = p[0], v01 = p[1], v10 = p[P], v11 = p[P + 1];
+    float top = fmaf(au, v01 - v00, v00);
+    float bot = fmaf(au, v11 - v10, v10);
+    return fmaf(aw, bot - top, top);
+}
+
+// Transpose of bilerp_padded: add g times each bilinear weight to the four
+// neighbours (non-atomic read-modify-write; callers guarantee that no two
+// threads touch the same pixel concurrently).
+__device__ __forceinline__ void scatter_padded(float* img, int P, int n, float u, float w, float g) {
+    if (!inside_open(u, w, n)) return;
+    float fj = floorf(u), fi = floorf(w);
+    float au = u - fj, aw = w - fi;
+    float* p = img + ((int)fi + 1) * P + ((int)fj + 1);
+    float g1 = g * aw, g0 = g - g1;          // row weights (1 - aw), aw
+    float g01 = g0 * au, g00 = g0 - g01;     // (1-aw)(1-au), (1-aw) au
+    float g11 = g1 * au, g10 = g1 - g11;     // aw (1-au), aw au
+    p[0] += g00;
+    p[1] += g01;
+    p[P] += g10;
+    p[P + 1] += g11;
+}
+
+// Bilinear sample of an unpadded global-memory image with per-neighbour
+// bounds checks (plain kernels).
+__device__ __forceinline__ float bilerp_global(const float* __restrict__ img, int n, float u, float w) {
+    if (!inside_open(u, w, n)) return 0.0f;
+    float fj = floorf(u), fi = floorf(w);
+    float au = u - fj, aw = w - fi;
+    int j0 = (int)fj, i0 = (int)fi;
+    float v00 = 0.f, v01 = 0.f, v10 = 0.f, v11 = 0.f;
+    bool jl = j0 >= 0, jh = j0 + 1 < n, il = i0 >= 0, ih = i0 + 1 < n;
+    if (il && jl) v00 = __ldg(img + i0 * n + j0);
+    if (il && jh) v01 = __ldg(img + i0 * n + j0 + 1);
+    if (ih && jl) v10 = __ldg(img + (i0 + 1) * n + j0);
+    if (ih && jh) v11 = __ldg(img + (i0 + 1) * n + j0 + 1);
+    float top = fmaf(au, v01 - v00, v00);
+    float bot = fmaf(au, v11 - v10, v10);
+    return fmaf(aw, bot - top, top);
+}
+
+// Bilinear weight with which ray sample (u, w) reads pixel (i, j): the same
+// products as scatter_padded (exact transpose of the forward weights).
+__device__ __forceinline__ float pixel_weight(float u, float w, int i, int j, int n) {
+    if (!inside_open(u, w, n)) return 0.0f;
+    float fj = floorf(u), fi = floorf(w);
+    int j0 = (int)fj, i0 = (int)fi;
+    int dj = j - j0, di = i - i0;
+    if ((unsigned)dj > 1u || (unsigned)di > 1u) return 0.0f;
+    float au = u - fj, aw = w - fi;
+    float r = di ? aw : 1.0f - aw;
+    float cw = dj ? au : 1.0f - au;
+    return r * cw;
+}
+
+}  // namespace boac

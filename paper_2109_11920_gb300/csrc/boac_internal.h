@@ -1,0 +1,39 @@
+// boac_internal.h -- host-side helpers shared by the library's .cu files.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/boac.h"
+
+namespace boac {
+
+// Largest supported image side and view count.
+constexpr int kMaxN = 256;
+constexpr int kMaxViews = 720;
+
+// Geometry checks shared by every entry point: n in [8, kMaxN], n_bins == n,
+// bin_cm == pixel_cm > 0, n_views in [1, kMaxViews].
+bool geom_ok(const boac_geom* g);
+
+// Number of SMs of the current device (cached per device).
+int sm_count();
+
+// cudaStream_t from the ABI's void*.
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Map the last CUDA error to a status code (clears it).
+int launch_status();
+
+// Round up to a multiple of 256 bytes.
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Plain path: workspace for one candidate (table, sens, bp, q, r).
+size_t plain_candidate_bytes(const boac_geom* g);
+
+// Fused MLEM: resident CTA slots and workspace for geometry g and B candidates.
+int fused_slots(const boac_geom* g, int B);
+size_t fused_workspace_bytes(const boac_geom* g, int B);
+
+}  // namespace boac

@@ -1,0 +1,191 @@
+"""CUDA path vs the FP64 oracle, element by element, on seeded inputs built
+by the oracle (tests/problems.py).  Tolerances (relative L2 unless stated):
+one projection or back-projection 1e-5; MLEM images 1e-4; the float64 score
+reduction 1e-9 given the same q.  Marked gpu: run with ``-m gpu``."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2109_11920_gb300 import Geom, Tissue, synth
+from paper_2109_11920_gb300 import api as boac
+from problems import make_problem, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+# (n, dx, V): the three image classes of the workloads, plus small odd shapes
+SHAPES = [(64, 0.4, 60), (96, 25.6 / 96, 90), (128, 0.2, 120)]
+ODD = [(33, 0.7, 7), (20, 1.1, 4)]
+
+
+def T(x, dev, dtype=torch.float32):
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=dtype, device=dev)
+
+
+def geom(p):
+    return Geom.make(p.n, p.dx, p.V)
+
+
+@pytest.fixture(scope="module")
+def probs():
+    return {s: make_problem(*s, counts=2e5, B=3, seed=11) for s in SHAPES + ODD}
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("mode", [oracle.CENTER, oracle.AREA])
+def test_rasterize(cuda, shape, mode):
+    n, dx, V = shape
+    p = make_problem(n, dx, V, 1e5, B=8, seed=3, mode=mode)
+    mu = boac.boac_rasterize_mu(geom(p), Tissue(*p.tissue), T(p.coefs, cuda), mode).cpu().numpy()
+    ref = p.mu
+    if mode == oracle.CENTER:
+        # identical classes except where r is within 1e-9 cm of a boundary
+        assert np.mean(mu == ref.astype(np.float32)) > 1 - 1e-4
+        assert np.array_equal(np.unique(mu), np.unique(ref.astype(np.float32)))
+    else:
+        np.testing.assert_allclose(mu, ref, rtol=1e-6, atol=1e-7)
+
+
+@pytest.mark.parametrize("shape", SHAPES + ODD)
+def test_project(cuda, probs, shape):
+    p = probs[shape]
+    g = p.geom
+    rng = np.random.default_rng(1)
+    F = np.stack([p.F_true, rng.uniform(0, 2, (p.n, p.n)), np.ones((p.n, p.n))])
+    q = boac.boac_project(geom(p), T(p.mu, cuda), T(F, cuda)).cpu().numpy()
+    for b in range(3):
+        assert rel_l2(q[b], oracle.project(g, p.mu[b], F[b])) < 1e-5
+
+
+@pytest.mark.parametrize("shape", SHAPES + ODD)
+def test_backproject(cuda, probs, shape):
+    p = probs[shape]
+    g = p.geom
+    rng = np.random.default_rng(2)
+    y = np.stack([p.S, rng.uniform(0, 3, (p.V, p.n)), np.ones((p.V, p.n))])
+    out = boac.boac_backproject(geom(p), T(p.mu, cuda), T(y, cuda)).cpu().numpy()
+    sens = boac.boac_backproject(geom(p), T(p.mu, cuda), None).cpu().numpy()
+    for b in range(3):
+        assert rel_l2(out[b], oracle.backproject(g, p.mu[b], y[b])) < 1e-5
+        assert rel_l2(sens[b], oracle.sensitivity(g, p.mu[b])) < 1e-5
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_adjointness_fp32(cuda, probs, shape):
+    """<A x, y> = <x, A^T y> for the CUDA pair itself (float32 rounding)."""
+    p = probs[shape]
+    rng = np.random.default_rng(3)
+    x = T(rng.uniform(0, 1, (3, p.n, p.n)), cuda)
+    y = T(rng.uniform(0, 1, (3, p.V, p.n)), cuda)
+    mu = T(p.mu, cuda)
+    lhs = (boac.boac_project(geom(p), mu, x).double() * y.double()).sum()
+    rhs = (x.double() * boac.boac_backproject(geom(p), mu, y).double()).sum()
+    assert abs(lhs - rhs) / abs(lhs) < 2e-6
+
+
+def run_mlem(p, dev, K, plain, B=None, S=None):
+    mu = T(p.mu if B is None else p.mu[:B], dev)
+    Bn = mu.shape[0]
+    F = torch.ones(Bn, p.n, p.n, dtype=torch.float32, device=dev)
+    S = T(p.S if S is None else S, dev)
+    F, L = boac.boac_mlem(geom(p), mu, S, F, K, score=True, plain=plain)
+    return F.cpu().numpy(), L.cpu().numpy()
+
+
+@pytest.mark.parametrize("plain", [False, True])
+@pytest.mark.parametrize("shape", [SHAPES[0], SHAPES[1]])
+def test_mlem_small(cuda, probs, shape, plain):
+    """20 iterations on the 64 and 96 classes: images within 1e-4, scores
+    (float64 reduction of a float32 projection) within 1e-6 relative."""
+    p = probs[shape]
+    K = 20
+    F, L = run_mlem(p, cuda, K, plain)
+    Fo, Lo, _ = oracle.mlem_batch(p.geom, p.mu, p.S, K)
+    for b in range(p.mu.shape[0]):
+        assert rel_l2(F[b], Fo[b]) < 1e-4, b
+        assert abs(L[b] - Lo[b]) < 1e-6 * abs(Lo[b])
+
+
+def test_fused_equals_plain(cuda, probs):
+    p = probs[SHAPES[2]]
+    F1, L1 = run_mlem(p, cuda, 10, plain=False)
+    F2, L2 = run_mlem(p, cuda, 10, plain=True)
+    assert rel_l2(F1, F2) < 2e-5
+    np.testing.assert_allclose(L1, L2, rtol=1e-7)
+
+
+def test_loglik_reduction_given_same_q(cuda, probs):
+    """The float64 reduction of Eq. 5 matches the oracle's to 1e-9 on the
+    same (float32) expected counts."""
+    p = probs[SHAPES[2]]
+    rng = np.random.default_rng(4)
+    q = rng.uniform(0.0, 50.0, (3, p.V, p.n)).astype(np.float32)
+    q[0, :, :5] = 0.0  # S = 0 there?  force S = 0 where q = 0 below
+    S = np.stack([p.S, rng.poisson(q[1]).astype(float), rng.poisson(q[2]).astype(float)])
+    S[0, :, :5] = 0.0
+    for lg in (True, False):
+        L = boac.boac_loglik(geom(p), T(q, cuda), T(S, cuda), include_lgamma=lg).cpu().numpy()
+        for b in range(3):
+            ref = oracle.loglik(S[b], q[b].astype(np.float64), lg)
+            assert abs(L[b] - ref) <= 1e-9 * abs(ref)
+    # q = 0 < S gives -inf
+    q[2, 0, 0] = 0.0
+    S[2, 0, 0] = 5.0
+    L = boac.boac_loglik(geom(p), T(q, cuda), T(S, cuda)).cpu().numpy()
+    assert L[2] == -np.inf and np.isfinite(L[1])
+
+
+def test_score_matches_oracle(cuda, probs):
+    p = probs[SHAPES[2]]
+    F = np.stack([p.F_true, 0.5 * p.F_true + 0.1, np.ones((p.n, p.n))])
+    L = boac.boac_score(geom(p), T(p.mu, cuda), T(p.S, cuda), T(F, cuda)).cpu().numpy()
+    for b in range(3):
+        ref = oracle.score(p.geom, p.mu[b], p.S, F[b])
+        assert abs(L[b] - ref) < 1e-6 * abs(ref)
+
+
+def test_edge_cases(cuda, probs):
+    p = probs[SHAPES[0]]
+    g = geom(p)
+    mu = T(p.mu, cuda)
+    S = T(p.S, cuda)
+    # K = 0 leaves F unchanged and scores F^0
+    F0 = torch.rand(3, p.n, p.n, device=cuda)
+    F, L = boac.boac_mlem(g, mu, S, F0.clone(), 0)
+    assert torch.equal(F, F0)
+    Lref = boac.boac_score(g, mu, S, F0)
+    torch.testing.assert_close(L, Lref, rtol=1e-7, atol=0)
+    # all-zero sinogram: r = 0 -> F = 0 after one iteration, L = -sum q = 0
+    F, L = boac.boac_mlem(g, mu, torch.zeros_like(S), torch.ones(3, p.n, p.n, device=cuda), 1)
+    assert float(F.abs().max()) == 0.0 and float(L.abs().max()) == 0.0
+    # mu = 0 (no attenuation correction) runs and matches the oracle
+    mu0 = torch.zeros_like(mu)
+    F, L = boac.boac_mlem(g, mu0, S, torch.ones(3, p.n, p.n, device=cuda), 5)
+    Fo = oracle.mlem(p.geom, np.zeros((p.n, p.n)), p.S, 5)
+    assert rel_l2(F[0].cpu().numpy(), Fo) < 1e-4
+    # per-candidate sinograms (s_stride != 0)
+    S3 = torch.stack([S, 2 * S, S.flip(-1)]).contiguous()
+    F, L = boac.boac_mlem(g, mu, S3, torch.ones(3, p.n, p.n, device=cuda), 4)
+    Fo1 = oracle.mlem(p.geom, p.mu[1], 2 * p.S, 4)
+    assert rel_l2(F[1].cpu().numpy(), Fo1) < 1e-4
+    # too small a workspace is refused, nothing launched
+    ws = torch.empty(16, dtype=torch.uint8, device=cuda)
+    with pytest.raises(Exception, match="workspace"):
+        boac.boac_mlem(g, mu, S, torch.ones(3, p.n, p.n, device=cuda), 2, ws=ws)
+
+
+def test_mlem_batched_full_size_sampled(cuda):
+    """The batched workload at full size (128^2, 120 views, 256 candidates,
+    50 iterations, one launch as the benchmark times it); candidates from the
+    first and second pass of the persistent grid and the last one checked
+    against the oracle."""
+    wl = synth.BATCHED
+    p = make_problem(wl.n, wl.dx, wl.V, wl.counts, B=wl.B, seed=wl.seed)
+    F, L = run_mlem(p, cuda, wl.K, plain=False)
+    nsm = torch.cuda.get_device_properties(cuda).multi_processor_count
+    picks = sorted({0, min(nsm, wl.B - 1), wl.B - 1})
+    Fo, Lo, _ = oracle.mlem_batch(p.geom, p.mu[picks], p.S, wl.K)
+    for i, b in enumerate(picks):
+        assert rel_l2(F[b], Fo[i]) < 1e-4, b
+        assert abs(L[b] - Lo[i]) < 1e-6 * abs(Lo[i]), b
+    assert np.all(np.isfinite(L)) and np.all(F >= 0)
