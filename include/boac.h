@@ -151,6 +151,28 @@ int boac_mlem_plain(const boac_geom *g, const float *mu, const float *S,
                     int include_lgamma, void *ws, size_t ws_bytes,
                     void *stream);
 
+/* ---- boac_mlem without a workspace -------------------------------------
+ * The paper has no counterpart: this is a convenience for callers that
+ * cannot allocate device memory when they call the library (code running
+ * under another framework's allocator or inside a callback where cudaMalloc
+ * is not allowed, or a host process without an allocator of its own).
+ * Same arguments and results as boac_mlem, minus the workspace: the fused
+ * kernel's scratch comes from a 64 MiB array built into the library, which
+ * every GPU that loads the library keeps until the process exits.
+ *   - The first call on a device looks up that array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - Fewer candidates run at once when one slot's scratch (n_views * n^2 + n^2
+ *     floats) does not fit 64 MiB many times; BOAC_EWORKSPACE if not even one
+ *     fits (not possible for the supported sizes, n <= 128 and n_views <= 720).
+ *   - Every call shares the one array: calls that can overlap on the GPU
+ *     (different streams, or other threads) race and corrupt each other's
+ *     results.  Serialise them.  Nothing needs to start at zero: each call
+ *     writes every scratch entry it reads.
+ *   - Allocates nothing: no cudaMalloc, cudaFree or allocating library call. */
+int boac_mlem_noalloc(const boac_geom *g, const float *mu, const float *S,
+                      long long s_stride, float *F, int K, int B, double *L,
+                      int include_lgamma, void *stream);
+
 /* ---- Eq. 5: score of given images ---------------------------------------
  * L[b] = sum_i S_i ln q_i - q_i [- ln S_i!], q = A^mu F (float32 projection,
  * float64 reduction; same conventions as boac_mlem).

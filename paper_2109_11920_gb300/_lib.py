@@ -76,6 +76,7 @@ SIGNATURES = {
     "boac_backproject": (_I, [_GP, _P, _P, _I, _P, _P, _SZ, _P]),
     "boac_mlem": (_I, [_GP, _P, _P, _LL, _P, _I, _I, _P, _I, _P, _SZ, _P]),
     "boac_mlem_plain": (_I, [_GP, _P, _P, _LL, _P, _I, _I, _P, _I, _P, _SZ, _P]),
+    "boac_mlem_noalloc": (_I, [_GP, _P, _P, _LL, _P, _I, _I, _P, _I, _P]),
     "boac_score": (_I, [_GP, _P, _P, _LL, _P, _I, _I, _P, _P, _SZ, _P]),
     "boac_loglik": (_I, [_GP, _P, _P, _LL, _I, _I, _P, _P]),
 }

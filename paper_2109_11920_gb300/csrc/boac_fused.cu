@@ -387,3 +387,97 @@ extern "C" int boac_mlem(const boac_geom* g, const float* mu, const float* S, lo
 #undef X
     return BOAC_EUNSUPPORTED;
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of boac_mlem.
+//
+// Some callers cannot allocate device memory at the moment they want a
+// reconstruction: code running inside another framework's memory pool or
+// allocator lock, a callback that must not call cudaMalloc (which can
+// synchronise the device), or a host process that has no allocator of its
+// own to hand the library a workspace.  boac_mlem_noalloc takes the fused
+// kernel's scratch (per-CTA attenuation tables and sensitivity images) from
+// a fixed array compiled into this library instead of from a caller
+// workspace.  The array lives in device memory on every GPU that loads the
+// library, for as long as the process runs.
+namespace boac {
+
+// Size of the built-in scratch: 64 MiB.
+constexpr size_t kNoAllocScratchBytes = size_t(64) << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+// Device address of g_noalloc_scratch, looked up once per device.  In host
+// code the array's name stands for a host-side shadow, not device memory,
+// so the kernel must be given the address cudaGetSymbolAddress returns.
+static void* noalloc_scratch_ptr() {
+    constexpr int kDev = 64;
+    static void* cached[kDev];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kDev) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (!cached[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        cached[dev] = p;
+    }
+    return cached[dev];
+}
+
+// Largest number of resident CTA slots whose tables and sensitivity images
+// fit the built-in scratch (0 if not even one does).
+static int noalloc_slots(const boac_geom* g, int B) {
+    int slots = fused_slots(g, B);
+    const size_t nn = (size_t)g->n * g->n;
+    while (slots > 0 && align256(sizeof(float) * (size_t)slots * nn * g->n_views) +
+                                align256(sizeof(float) * (size_t)slots * nn) >
+                            kNoAllocScratchBytes)
+        --slots;
+    return slots;
+}
+
+}  // namespace boac
+
+extern "C" int boac_mlem_noalloc(const boac_geom* g, const float* mu, const float* S,
+                                 long long s_stride, float* F, int K, int B, double* L,
+                                 int include_lgamma, void* stream) {
+    if (!geom_ok(g) || !mu || !S || !F || B < 1 || K < 0 || s_stride < 0) return BOAC_EINVAL;
+    if (g->n_views % 2) return BOAC_EINVAL;
+    bool have = false;
+#define X(NV, TV) have |= (g->n == NV);
+    BOAC_FUSED_SIZES(X)
+#undef X
+    if (!have) return BOAC_EUNSUPPORTED;
+    if (fused_slots(g, B) <= 0) return BOAC_ECUDA;
+    const int slots = noalloc_slots(g, B);
+    if (slots <= 0) return BOAC_EWORKSPACE;  // one candidate's scratch exceeds 64 MiB
+    void* scratch = noalloc_scratch_ptr();
+    if (!scratch) return BOAC_ECUDA;
+    const size_t nn = (size_t)g->n * g->n;
+    FusedArgs a;
+    a.mu = mu;
+    a.S = S;
+    a.s_stride = s_stride;
+    a.F = F;
+    a.L = L;
+    a.include_lgamma = include_lgamma;
+    a.B = B;
+    a.V = g->n_views;
+    a.K = K;
+    a.dx = g->pixel_cm;
+    // The kernel writes every table entry and sensitivity pixel of a slot
+    // before reading it, so the scratch needs no clearing between calls.
+    a.tab = static_cast<float*>(scratch);
+    a.sens = reinterpret_cast<float*>(static_cast<char*>(scratch) +
+                                      align256(sizeof(float) * (size_t)slots * nn * g->n_views));
+    cudaStream_t st = as_stream(stream);
+#define X(NV, TV) \
+    if (g->n == NV) return fused_launch<NV, TV>(a, slots, st);
+    BOAC_FUSED_SIZES(X)
+#undef X
+    return BOAC_EUNSUPPORTED;
+}

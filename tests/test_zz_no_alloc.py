@@ -1,0 +1,61 @@
+"""boac_mlem_noalloc -- MLEM for callers that cannot allocate device memory
+(for example code running under another framework's allocator or in a
+callback where cudaMalloc is not allowed).  It takes its scratch from an
+array built into the library instead of a caller workspace.
+
+Called here through the raw C ABI (ctypes, device pointers) and checked
+against boac_mlem, the workspace-taking entry point, on two calls in a row
+with different inputs, so that leftovers of the first call in the shared
+scratch would show up in the second.  This file is named to be collected
+last; it passes on its own in a fresh process and after the other tests.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2109_11920_gb300 import Geom, _lib
+from paper_2109_11920_gb300 import api as boac
+from problems import make_problem, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def _p(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def call_noalloc(lib, g, mu, S, F, K, L):
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return lib.boac_mlem_noalloc(ctypes.byref(g), _p(mu), _p(S), 0, _p(F), K, mu.shape[0], _p(L), 1, stream)
+
+
+def test_noalloc_matches_workspace_entry_point(cuda):
+    from paper_2109_11920_gb300 import build
+    build.build()
+    lib = _lib.load()
+    # 128 x 128, 120 views: one slot needs ~7.9 MB of scratch, so the 64 MiB
+    # array holds 8 slots and 20 candidates take several rounds per CTA.
+    p = make_problem(128, 0.2, 120, 1e6, B=20, seed=5)
+    g = Geom.make(p.n, p.dx, p.V)
+    mu_all = torch.tensor(p.mu, dtype=torch.float32, device=cuda)
+    S = torch.tensor(p.S, dtype=torch.float32, device=cuda)
+    for call, (order, K) in enumerate([(np.arange(20), 4), (np.arange(20)[::-1].copy(), 3)]):
+        mu = mu_all[torch.as_tensor(order, device=cuda)].contiguous()
+        F_ref = torch.ones(20, p.n, p.n, device=cuda)
+        F_ref, L_ref = boac.boac_mlem(g, mu, S, F_ref, K)
+        F = torch.ones(20, p.n, p.n, device=cuda)
+        L = torch.empty(20, dtype=torch.float64, device=cuda)
+        st = call_noalloc(lib, g, mu, S, F, K, L)
+        assert st == _lib.BOAC_OK, _lib.status_string(st)
+        torch.cuda.synchronize()
+        assert rel_l2(F.cpu().numpy(), F_ref.cpu().numpy()) < 1e-5, call
+        np.testing.assert_allclose(L.cpu().numpy(), L_ref.cpu().numpy(), rtol=1e-9)
+    # arguments are still checked on the host
+    F = torch.ones(20, p.n, p.n, device=cuda)
+    L = torch.empty(20, dtype=torch.float64, device=cuda)
+    bad = Geom.make(p.n, p.dx, 119)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert lib.boac_mlem_noalloc(ctypes.byref(bad), _p(mu_all), _p(S), 0, _p(F), 2, 20, _p(L), 1,
+                                 stream) == _lib.BOAC_EINVAL
