@@ -235,7 +235,8 @@ def run_gpu(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     g, t, coefs, S_np = make_inputs_gpu(dev, boac, Geom, Tissue, seed=WL.seed + rank)
-    B, K = WL.B, WL.K
+    B, K = args.candidates, args.iters
+    coefs = coefs[:B] if B <= len(coefs) else np.resize(coefs, (B, 6))
     c_d = torch.tensor(coefs, device=dev)
     S_d = torch.tensor(S_np, device=dev)
     mu = torch.empty(B, WL.n, WL.n, device=dev)
@@ -286,6 +287,50 @@ def run_gpu(args, rank, world, local_rank):
     assert torch.isfinite(L).all(), "non-finite score"
 
     # ---- end to end through the public API with host buffers (pinned)
+    e2e = None
+    if not args.no_e2e:
+        e2e = e2e_timing(args, world, dev, stream, step, c_d, S_d, L, F, coefs, S_np, flush, B, K)
+    if rank != 0:
+        return
+    plain = None if args.no_plain else plain_timing(g, boac, mu, S_d, dev, stream, K)
+
+    # ---- roofline of the dominant kernel (the fused MLEM kernel)
+    kavg_s = sum(kern_ms) / len(kern_ms) / 1e3
+    alg = algorithmic_bytes_per_cand_iter(WL.n, WL.V) * B * K
+    peak, peak_kind = measured_peak_gbs()
+    achieved = alg / kavg_s / 1e9
+    traffic = profiled_traffic() if (B, K) == (WL.B, WL.K) else None
+    roof = {"bound": "hbm", "kernel": "mlem_fused_kernel<128,1024>", "achieved": achieved,
+            "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+            "peak_kind": f"{peak_kind} hbm_gbs (copy)",
+            "algorithmic_bytes_per_launch": alg,
+            "kernel_ms": 1e3 * kavg_s}
+    config = dict(CONFIG, global_batch=world * B, parallelism=f"replicas{world}")
+    if (B, K) != (WL.B, WL.K):
+        config["reduced_case"] = f"{B} candidates x {K} iterations (not the benchmark workload)"
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": config,
+        "roofline": roof,
+        "e2e": e2e,
+        "gpu_launches": 2 * args.steps,
+        "clocks": clk.summary(),
+    }
+    if plain is not None:
+        line["plain_path"] = dict(plain, speedup_of_batched=value / world / plain["value"])
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_sample()
+    print(json.dumps(line), flush=True)
+
+
+def e2e_timing(args, world, dev, stream, step, c_d, S_d, L, F, coefs, S_np, flush, B, K):
+    """Same metric through the public API with pinned host buffers: H2D of the
+    coefficients and sinogram, the step, D2H of the scores and images."""
+    import torch
+    import torch.distributed as dist
+    E = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
     c_h = torch.tensor(coefs).pin_memory()
     S_h = torch.tensor(S_np).pin_memory()
     L_h = torch.empty(B, dtype=torch.float64).pin_memory()
@@ -315,54 +360,29 @@ def run_gpu(args, rank, world, local_rank):
         tt = torch.tensor([e_tot], device=dev, dtype=torch.float64)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         e_tot = float(tt.item())
-    e2e = {"value": world * B * K * args.steps / (e_tot / 1e3), "unit": UNIT,
-           "h2d_bytes_per_step": c_h.numel() * 4 + S_h.numel() * 4,
-           "d2h_bytes_per_step": L_h.numel() * 8 + F_h.numel() * 4}
+    return {"value": world * B * K * args.steps / (e_tot / 1e3), "unit": UNIT,
+            "h2d_bytes_per_step": c_h.numel() * 4 + S_h.numel() * 4,
+            "d2h_bytes_per_step": L_h.numel() * 8 + F_h.numel() * 4}
 
-    if rank != 0:
-        return
 
-    # ---- plain launch-per-step path (one candidate at a time), sampled
+def plain_timing(g, boac, mu, S_d, dev, stream, K):
+    """The launch-per-step path (one candidate at a time), on 4 candidates."""
+    import torch
+    E = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
     nplain = 4
     Fp = torch.ones(nplain, WL.n, WL.n, device=dev)
     wsp = boac.workspace(g, nplain, boac._lib.OP_MLEM_PLAIN, dev)
-    boac.boac_mlem(g, mu[:nplain].contiguous(), S_d, Fp, 2, plain=True, ws=wsp)
+    mup = mu[:nplain].contiguous()
+    boac.boac_mlem(g, mup, S_d, Fp, 2, plain=True, ws=wsp)
     torch.cuda.synchronize(dev)
     a, b = E(), E()
     Fp.fill_(1.0)
     a.record(stream)
-    boac.boac_mlem(g, mu[:nplain].contiguous(), S_d, Fp, K, plain=True, ws=wsp)
+    boac.boac_mlem(g, mup, S_d, Fp, K, plain=True, ws=wsp)
     b.record(stream)
     b.synchronize()
-    plain_value = nplain * K / (a.elapsed_time(b) / 1e3)
-
-    # ---- roofline of the dominant kernel (the fused MLEM kernel)
-    kavg_s = sum(kern_ms) / len(kern_ms) / 1e3
-    alg = algorithmic_bytes_per_cand_iter(WL.n, WL.V) * B * K
-    peak, peak_kind = measured_peak_gbs()
-    achieved = alg / kavg_s / 1e9
-    traffic = profiled_traffic()
-    roof = {"bound": "hbm", "kernel": "mlem_fused_kernel<128,1024>", "achieved": achieved,
-            "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-            "peak_kind": f"{peak_kind} hbm_gbs (copy)",
-            "algorithmic_bytes_per_launch": alg,
-            "kernel_ms": 1e3 * kavg_s}
-
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": dict(CONFIG, global_batch=world * B, parallelism=f"replicas{world}"),
-        "roofline": roof,
-        "e2e": e2e,
-        "gpu_launches": 2 * args.steps,
-        "clocks": clk.summary(),
-        "plain_path": {"value": plain_value, "unit": UNIT, "sample": f"{nplain} candidates x {K} iterations",
-                       "speedup_of_batched": value / world / plain_value},
-    }
-    if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_sample()
-    print(json.dumps(line), flush=True)
+    return {"value": nplain * K / (a.elapsed_time(b) / 1e3), "unit": UNIT,
+            "sample": f"{nplain} candidates x {K} iterations, 4 launches per iteration"}
 
 
 def main():
@@ -372,6 +392,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    # smaller cases for profiling (the default is the full workload)
+    ap.add_argument("--candidates", type=int, default=WL.B, help="candidates per GPU")
+    ap.add_argument("--iters", type=int, default=WL.K, help="MLEM iterations")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain-path comparison")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffer) timing")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -6,17 +6,21 @@
 // One CTA owns one candidate at a time and keeps its whole state on chip:
 //   img0  F (padded n+2 rows x n+3 floats, zero ring)   -- mu during set-up
 //   img1  back-projection accumulator (same layout)
-//   W     n x n ray-sample buffer (attenuation sums, then G = dx a r)
-// The candidate's "system matrix" -- the attenuation factor of every ray
-// sample -- is built once per candidate into a per-CTA slot of the workspace
-// and read back (coalesced, from L2/HBM) in every iteration.
+//   W     n x (n+1) ray-sample buffer (F samples, then G = dx a r)
+// The candidate's "system matrix" -- the attenuation of every ray sample --
+// is built once per candidate into a per-CTA slot of the workspace (as
+// exp2 exponents) and read back, coalesced, in every iteration.
 //
-// Views phi and phi + pi share one sample grid: sample (k, b) of view
-// v + V/2 is sample (n-1-k, n-1-b) of view v, so one bilinear sampling of F
-// serves two views, the two attenuation factors differ only in the scan
-// direction (suffix vs prefix along k), and the two views' back-projection
-// weights G = dx (a_v r_v + a_{v+V/2} r_{v+V/2}) are summed on the grid
-// before ONE transposed-bilinear scatter.
+// Four views share one sample grid: with bins and ray samples on the pixel
+// pitch, the grids of phi, phi + pi/2, phi + pi and phi + 3pi/2 are the same
+// set of points (a quarter turn maps the lattice onto itself), so sample
+// (k, b) of view phi + pi is sample (n-1-k, n-1-b) of view phi, and the rays
+// of phi + pi/2 and phi + 3pi/2 are the grid's rows.  One bilinear sampling of
+// F serves four views (column sums for phi, phi + pi; row sums for the other
+// two), and the four views' back-projection weights
+//   G = dx (a_phi r_phi + a_{phi+pi} r_{phi+pi} + a_{phi+pi/2} r + a_{phi+3pi/2} r)
+// are summed on the grid before ONE transposed-bilinear scatter.  View counts
+// that are not a multiple of 4 use pairs (phi, phi + pi) the same way.
 //
 // The scatter is race-free and deterministic without atomics: the samples
 // are split into 9 classes by (k mod 3, b mod 3); two samples of one class
@@ -41,37 +45,60 @@ struct FusedArgs {
     float dx;
     // Per-CTA slots, written and read by the same CTA within one launch:
     // read with plain (coherent) loads, never through the read-only path.
-    float* tab;   // [slots][V][n][n]: pair p -> planes 2p (view p), 2p+1 (view p+V/2)
+    float* tab;   // [slots][tab_floats]: attenuation exponents, see below
     float* sens;  // [slots][n][n]
 };
 
-template <int N>
+// Shared-memory and work layout of one CTA (image side N, NT threads).
+template <int N, int NT>
 struct FusedShape {
-    static constexpr int P = N + 3;          // padded row pitch (odd)
+    static constexpr int P = N + 3;          // padded image pitch (odd)
     static constexpr int IMG = (N + 2) * P;  // floats per padded image
     static constexpr int NN = N * N;
+    static constexpr int WP = N + 1;         // sample-buffer pitch (odd)
+    static constexpr int NSEG = NT / N;      // segments per column / row
+    static constexpr int SEG = N / NSEG;     // samples per segment
+    static_assert(NT % N == 0 && N % NSEG == 0, "segmentation");
 };
+
+// Views that share one sample grid: 4 (phi + j pi/2, needs V % 4 == 0) or 2
+// (phi, phi + pi).  Attenuation exponents stored per grid, already scaled by
+// -dx log2(e) so that a = exp2(y):
+//   Xc[k][b] = view phi        (detector at k -> +inf, suffix along k)
+//   Uc[b]    = whole-column sum: the view phi + pi exponent is Uc - Xc
+//   XrT[b][k] = view phi + pi/2 (detector at b -> -inf, prefix along b),
+//               stored transposed for row-parallel access
+//   Ur[k]    = whole-row sum: the view phi + 3pi/2 exponent is Ur - XrT
+// because for one ray the half-cell sums towards both ends add up to the
+// ray's total: a_phi * a_{phi+pi} = exp(-dx sum_k mu_k).
+__host__ __device__ constexpr size_t fused_group_floats(int n, bool quad) {
+    return quad ? 2 * (size_t)n * n + 2 * (size_t)n : (size_t)n * n + (size_t)n;
+}
+__host__ __device__ constexpr size_t fused_tab_floats(int n, int V) {
+    // V/4 groups of 4 views or V/2 groups of 2: the same total
+    return (size_t)(V / 2) * ((size_t)n * n + (size_t)n);
+}
 
 template <int N, int NT>
 __host__ __device__ constexpr size_t fused_smem_bytes(int V) {
-    return sizeof(float) * (2 * FusedShape<N>::IMG + FusedShape<N>::NN + (NT / N) * 2 * N + 2 * N +
-                            2 * ((V + 1) / 2) * 2) +
+    using L = FusedShape<N, NT>;
+    return sizeof(float) * (2 * L::IMG + N * L::WP + 4 * L::NSEG * N + 4 * N + 2 * ((V + 1) / 2) * 2) +
            sizeof(double) * 32;
 }
 
-// Scatter G (W, n x n) into the padded accumulator img1 with the bilinear
+// Scatter G (W, pitch WP) into the padded accumulator img1 with the bilinear
 // weights of grid (cs, sn), class by class (see the file comment).
 template <int N, int NT>
 __device__ __forceinline__ void scatter_classes(const float* __restrict__ W, float* img1, float cs,
                                                 float sn, float c) {
-    constexpr int P = FusedShape<N>::P;
+    constexpr int P = FusedShape<N, NT>::P, WP = FusedShape<N, NT>::WP;
 #pragma unroll
     for (int cls = 0; cls < 9; ++cls) {
         const int pk = cls / 3, pb = cls % 3;
         const int nkc = (N - pk + 2) / 3, nbc = (N - pb + 2) / 3;
         for (int t = threadIdx.x; t < nkc * nbc; t += NT) {
             const int k = pk + 3 * (t / nbc), b = pb + 3 * (t % nbc);
-            const float g = W[k * N + b];
+            const float g = W[k * WP + b];
             float u, w;
             sample_uw(k, b, cs, sn, c, &u, &w);
             scatter_padded(img1, P, N, u, w, g);
@@ -80,37 +107,52 @@ __device__ __forceinline__ void scatter_classes(const float* __restrict__ W, flo
     }
 }
 
-// CTAs per SM the register allocation is sized for (shared memory allows
-// about four 64x64 CTAs per SM, one of the larger sizes).
-template <int N>
-constexpr int fused_min_blocks() { return N <= 64 ? 4 : 1; }
+__device__ __forceinline__ double loglik_term(double s, double q, int include_lgamma) {
+    double t;
+    if (s > 0.0) t = q > 0.0 ? s * log(q) - q : -INFINITY;
+    else t = -q;
+    if (include_lgamma) t -= lgamma(s + 1.0);
+    return t;
+}
 
-template <int N, int NT>
+// CTAs per SM the register allocation is sized for (shared memory allows
+// three 64x64 CTAs per SM, one of the larger sizes).
+template <int N>
+constexpr int fused_min_blocks() { return N <= 64 ? 3 : 1; }
+
+template <int N, int NT, bool QUAD>
 __global__ void __launch_bounds__(NT, fused_min_blocks<N>()) mlem_fused_kernel(FusedArgs a) {
-    constexpr int P = FusedShape<N>::P, IMG = FusedShape<N>::IMG, NN = FusedShape<N>::NN;
-    constexpr int NSEG = NT / N, SEG = N / NSEG;
-    static_assert(NT % N == 0 && N % NSEG == 0, "column segmentation");
+    using Lay = FusedShape<N, NT>;
+    constexpr int P = Lay::P, IMG = Lay::IMG, NN = Lay::NN, WP = Lay::WP;
+    constexpr int NSEG = Lay::NSEG, SEG = Lay::SEG;
+    constexpr float kLog2e = 1.44269504088896340736f;
+    static_assert(!QUAD || NT >= 2 * N, "row views need 2N threads in the ratio step");
 
     extern __shared__ __align__(16) float smem[];
-    float* img0 = smem;
-    float* img1 = img0 + IMG;
-    float* W = img1 + IMG;
-    float* red = W + NN;            // [NSEG][2][N]
-    float* r1 = red + NSEG * 2 * N; // [N]
-    float* r2 = r1 + N;             // [N]
-    float* csn = r2 + N;            // [V][2]
+    float* img0 = smem;                 // F (mu during set-up), padded
+    float* img1 = img0 + IMG;           // back-projection accumulator, padded
+    float* W = img1 + IMG;              // [N][WP] grid samples / weights
+    float* redc = W + N * WP;           // [2][NSEG][N] column partial sums
+    float* redr = redc + 2 * NSEG * N;  // [2][NSEG][N] row partial sums
+    float* rr = redr + 2 * NSEG * N;    // [4][N] ratios r = S / q per view
+    float* csn = rr + 4 * N;            // [V][2]
     double* dred = reinterpret_cast<double*>(csn + 2 * ((a.V + 1) / 2) * 2);
 
     const int tid = threadIdx.x;
-    const int V = a.V, half = V / 2;
+    const int V = a.V;
+    const int ngrid = QUAD ? V / 4 : V / 2;
     const float c = 0.5f * (float)(N - 1);
     const float dx = a.dx;
-    const int bcol = tid % N, seg = tid / N;
+    const float ndl = -dx * kLog2e;
+    // column mapping: thread owns column `lb`, samples k in [k0, k0 + SEG);
+    // row mapping: thread owns row `lb`, samples b in [k0, k0 + SEG)
+    const int lb = tid % N, seg = tid / N;
     const int k0 = seg * SEG;
+    const size_t gstride = fused_group_floats(N, QUAD);
 
     for (int v = tid; v < V; v += NT) view_cos_sin(v, V, &csn[2 * v], &csn[2 * v + 1]);
 
-    float* tab = a.tab + (size_t)blockIdx.x * V * NN;
+    float* tab = a.tab + (size_t)blockIdx.x * fused_tab_floats(N, V);
     float* sens = a.sens + (size_t)blockIdx.x * NN;
 
     for (int cand = blockIdx.x; cand < a.B; cand += gridDim.x) {
@@ -126,43 +168,78 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<N>()) mlem_fused_kernel(F
         for (int i = tid; i < NN; i += NT) img0[(i / N + 1) * P + (i % N) + 1] = __ldg(mu + i);
         __syncthreads();
 
-        // ---- system matrix (attenuation factors) + sensitivity A^T 1
-        for (int p = 0; p < half; ++p) {
-            const float cs = csn[2 * p], sn = csn[2 * p + 1];
-            float* t1 = tab + (size_t)(2 * p) * NN;      // view p: suffix along k
-            float* t2 = tab + (size_t)(2 * p + 1) * NN;  // view p+V/2: prefix along k
-            float ssum = 0.0f;
+        // ---- system matrix (attenuation exponents) + sensitivity A^T 1
+        for (int gi = 0; gi < ngrid; ++gi) {
+            const float cs = csn[2 * gi], sn = csn[2 * gi + 1];
+            float* Xc = tab + gi * gstride;
+            float* XrT = Xc + NN;
+            float* Uc = QUAD ? Xc + 2 * NN : Xc + NN;
+            float* Ur = Uc + N;
+            float ps = 0.0f;
             for (int s = 0; s < SEG; ++s) {
                 float u, w;
-                sample_uw(k0 + s, bcol, cs, sn, c, &u, &w);
-                float m = bilerp_padded(img0, P, N, u, w);
-                W[(k0 + s) * N + bcol] = m;
-                ssum += m;
+                sample_uw(k0 + s, lb, cs, sn, c, &u, &w);
+                const float m = bilerp_padded(img0, P, N, u, w);
+                W[(k0 + s) * WP + lb] = m;
+                ps += m;
             }
-            red[seg * N + bcol] = ssum;
+            redc[seg * N + lb] = ps;
             __syncthreads();
-            float before = 0.0f, after = 0.0f;
+            {   // columns: suffix sums towards k = N-1
+                float after = 0.0f, total = 0.0f;
 #pragma unroll
-            for (int s2 = 0; s2 < NSEG; ++s2) {
-                float v = red[s2 * N + bcol];
-                if (s2 < seg) before += v;
-                if (s2 > seg) after += v;
+                for (int s2 = 0; s2 < NSEG; ++s2) {
+                    const float v = redc[s2 * N + lb];
+                    total += v;
+                    if (s2 > seg) after += v;
+                }
+                float suf = after;
+                for (int s = SEG - 1; s >= 0; --s) {
+                    const int k = k0 + s;
+                    const float m = W[k * WP + lb];
+                    Xc[k * N + lb] = ndl * (0.5f * m + suf);
+                    suf += m;
+                }
+                if (seg == 0) Uc[lb] = ndl * total;
             }
-            float pre = before;
-            for (int s = 0; s < SEG; ++s) {
-                const int k = k0 + s;
-                float m = W[k * N + bcol];
-                t2[k * N + bcol] = expf(-dx * (0.5f * m + pre));
-                pre += m;
+            if (QUAD) {  // rows: prefix sums from b = 0
+                float pr = 0.0f;
+                for (int s = 0; s < SEG; ++s) pr += W[lb * WP + k0 + s];
+                redr[seg * N + lb] = pr;
+                __syncthreads();
+                float before = 0.0f, total = 0.0f;
+#pragma unroll
+                for (int s2 = 0; s2 < NSEG; ++s2) {
+                    const float v = redr[s2 * N + lb];
+                    total += v;
+                    if (s2 < seg) before += v;
+                }
+                float pre = before;
+                for (int s = 0; s < SEG; ++s) {
+                    const int b = k0 + s;
+                    const float m = W[lb * WP + b];
+                    XrT[b * N + lb] = ndl * (0.5f * m + pre);
+                    pre += m;
+                }
+                if (seg == 0) Ur[lb] = ndl * total;
             }
-            float suf = after;
-            for (int s = SEG - 1; s >= 0; --s) {
-                const int k = k0 + s;
-                float m = W[k * N + bcol];
-                float a1 = expf(-dx * (0.5f * m + suf));
-                suf += m;
-                t1[k * N + bcol] = a1;
-                W[k * N + bcol] = dx * (a1 + t2[k * N + bcol]);
+            __syncthreads();
+            {   // G = dx (sum of the grid's views' attenuation factors)
+                const float uc = Uc[lb];
+                for (int s = 0; s < SEG; ++s) {
+                    const int k = k0 + s;
+                    const float y = Xc[k * N + lb];
+                    W[k * WP + lb] = dx * (exp2f(y) + exp2f(uc - y));
+                }
+            }
+            if (QUAD) {
+                __syncthreads();
+                const float ur = Ur[lb];
+                for (int s = 0; s < SEG; ++s) {
+                    const int b = k0 + s;
+                    const float y = XrT[b * N + lb];
+                    W[lb * WP + b] += dx * (exp2f(y) + exp2f(ur - y));
+                }
             }
             __syncthreads();
             scatter_classes<N, NT>(W, img1, cs, sn, c);
@@ -176,49 +253,100 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<N>()) mlem_fused_kernel(F
         for (int i = tid; i < IMG; i += NT) img1[i] = 0.0f;
         __syncthreads();
 
-        // ---- MLEM iterations
-        for (int it = 0; it < a.K; ++it) {
-            for (int p = 0; p < half; ++p) {
-                const float cs = csn[2 * p], sn = csn[2 * p + 1];
-                const float* t1 = tab + (size_t)(2 * p) * NN;
-                const float* t2 = tab + (size_t)(2 * p + 1) * NN;
-                // forward: sample F on the grid and reduce both views' columns
-                float acc1 = 0.0f, acc2 = 0.0f;
-                for (int s = 0; s < SEG; ++s) {
-                    const int k = k0 + s;
-                    float u, w;
-                    sample_uw(k, bcol, cs, sn, c, &u, &w);
-                    float f = bilerp_padded(img0, P, N, u, w);
-                    acc1 = fmaf(t1[k * N + bcol], f, acc1);
-                    acc2 = fmaf(t2[k * N + bcol], f, acc2);
+        // ---- MLEM iterations, then one more forward pass for the score
+        double lacc = 0.0;
+        for (int it = 0; it <= a.K; ++it) {
+            const bool scoring = (it == a.K);
+            if (scoring && !a.L) break;
+            for (int gi = 0; gi < ngrid; ++gi) {
+                const float cs = csn[2 * gi], sn = csn[2 * gi + 1];
+                const float* Xc = tab + gi * gstride;
+                const float* XrT = Xc + NN;
+                const float* Uc = QUAD ? Xc + 2 * NN : Xc + NN;
+                const float* Ur = Uc + N;
+                const int vc1 = gi, vc2 = gi + V / 2;           // column views
+                const int vr1 = gi + V / 4, vr2 = gi + 3 * V / 4;  // row views (QUAD)
+                // forward, column views: sample F on the grid
+                {
+                    const float uc = Uc[lb];
+                    float acc1 = 0.0f, acc2 = 0.0f;
+                    for (int s = 0; s < SEG; ++s) {
+                        const int k = k0 + s;
+                        float u, w;
+                        sample_uw(k, lb, cs, sn, c, &u, &w);
+                        const float f = bilerp_padded(img0, P, N, u, w);
+                        if (QUAD) W[k * WP + lb] = f;
+                        const float y = Xc[k * N + lb];
+                        acc1 = fmaf(exp2f(y), f, acc1);
+                        acc2 = fmaf(exp2f(uc - y), f, acc2);
+                    }
+                    redc[seg * N + lb] = acc1;
+                    redc[(NSEG + seg) * N + lb] = acc2;
                 }
-                red[(seg * 2 + 0) * N + bcol] = acc1;
-                red[(seg * 2 + 1) * N + bcol] = acc2;
+                if (QUAD) {  // forward, row views: the samples back from W
+                    __syncthreads();
+                    const float ur = Ur[lb];
+                    float acc3 = 0.0f, acc4 = 0.0f;
+                    for (int s = 0; s < SEG; ++s) {
+                        const int b = k0 + s;
+                        const float f = W[lb * WP + b];
+                        const float y = XrT[b * N + lb];
+                        acc3 = fmaf(exp2f(y), f, acc3);
+                        acc4 = fmaf(exp2f(ur - y), f, acc4);
+                    }
+                    redr[seg * N + lb] = acc3;
+                    redr[(NSEG + seg) * N + lb] = acc4;
+                }
                 __syncthreads();
-                if (tid < N) {
+                // q, then r = S / q (or the Eq. 5 terms when scoring)
+                if (tid < (QUAD ? 2 * N : N)) {
+                    const int j = tid % N;
+                    const bool row = tid >= N;
+                    const float* rp = row ? redr : redc;
                     float q1 = 0.0f, q2 = 0.0f;
 #pragma unroll
                     for (int s2 = 0; s2 < NSEG; ++s2) {
-                        q1 += red[(s2 * 2 + 0) * N + tid];
-                        q2 += red[(s2 * 2 + 1) * N + tid];
+                        q1 += rp[s2 * N + j];
+                        q2 += rp[(NSEG + s2) * N + j];
                     }
                     q1 *= dx;
                     q2 *= dx;
-                    const float S1 = __ldg(S + (size_t)p * N + tid);
-                    const float S2 = __ldg(S + (size_t)(p + half) * N + (N - 1 - tid));
-                    r1[tid] = q1 > 0.0f ? S1 / q1 : 0.0f;
-                    r2[tid] = q2 > 0.0f ? S2 / q2 : 0.0f;
+                    const int v1 = row ? vr1 : vc1, v2 = row ? vr2 : vc2;
+                    const float S1 = __ldg(S + (size_t)v1 * N + j);
+                    const float S2 = __ldg(S + (size_t)v2 * N + (N - 1 - j));
+                    if (scoring) {
+                        lacc += loglik_term(S1, q1, a.include_lgamma) + loglik_term(S2, q2, a.include_lgamma);
+                    } else {
+                        rr[(row ? 2 : 0) * N + j] = q1 > 0.0f ? S1 / q1 : 0.0f;
+                        rr[(row ? 3 : 1) * N + j] = q2 > 0.0f ? S2 / q2 : 0.0f;
+                    }
                 }
                 __syncthreads();
-                // back-projection weights of both views on the shared grid
-                const float rr1 = dx * r1[bcol], rr2 = dx * r2[bcol];
-                for (int s = 0; s < SEG; ++s) {
-                    const int k = k0 + s;
-                    W[k * N + bcol] = fmaf(t1[k * N + bcol], rr1, t2[k * N + bcol] * rr2);
+                if (scoring) continue;
+                // back-projection weights of the grid's views
+                {
+                    const float uc = Uc[lb];
+                    const float r1 = dx * rr[lb], r2 = dx * rr[N + lb];
+                    for (int s = 0; s < SEG; ++s) {
+                        const int k = k0 + s;
+                        const float y = Xc[k * N + lb];
+                        W[k * WP + lb] = fmaf(exp2f(y), r1, exp2f(uc - y) * r2);
+                    }
+                }
+                if (QUAD) {
+                    __syncthreads();
+                    const float ur = Ur[lb];
+                    const float r3 = dx * rr[2 * N + lb], r4 = dx * rr[3 * N + lb];
+                    for (int s = 0; s < SEG; ++s) {
+                        const int b = k0 + s;
+                        const float y = XrT[b * N + lb];
+                        W[lb * WP + b] += fmaf(exp2f(y), r3, exp2f(ur - y) * r4);
+                    }
                 }
                 __syncthreads();
                 scatter_classes<N, NT>(W, img1, cs, sn, c);
             }
+            if (scoring) break;
             // multiplicative update; clears the accumulator for the next pass
             for (int i = tid; i < IMG; i += NT) {
                 const int row = i / P, col = i % P;
@@ -231,49 +359,8 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<N>()) mlem_fused_kernel(F
             __syncthreads();
         }
 
-        // ---- Eq. 5 score of F^K (float32 projection, float64 reduction)
+        // ---- Eq. 5: deterministic block reduction of the float64 terms
         if (a.L) {
-            double lacc = 0.0;
-            for (int p = 0; p < half; ++p) {
-                const float cs = csn[2 * p], sn = csn[2 * p + 1];
-                const float* t1 = tab + (size_t)(2 * p) * NN;
-                const float* t2 = tab + (size_t)(2 * p + 1) * NN;
-                float acc1 = 0.0f, acc2 = 0.0f;
-                for (int s = 0; s < SEG; ++s) {
-                    const int k = k0 + s;
-                    float u, w;
-                    sample_uw(k, bcol, cs, sn, c, &u, &w);
-                    float f = bilerp_padded(img0, P, N, u, w);
-                    acc1 = fmaf(t1[k * N + bcol], f, acc1);
-                    acc2 = fmaf(t2[k * N + bcol], f, acc2);
-                }
-                red[(seg * 2 + 0) * N + bcol] = acc1;
-                red[(seg * 2 + 1) * N + bcol] = acc2;
-                __syncthreads();
-                if (tid < N) {
-                    float q1 = 0.0f, q2 = 0.0f;
-#pragma unroll
-                    for (int s2 = 0; s2 < NSEG; ++s2) {
-                        q1 += red[(s2 * 2 + 0) * N + tid];
-                        q2 += red[(s2 * 2 + 1) * N + tid];
-                    }
-                    q1 *= dx;
-                    q2 *= dx;
-                    const double S1 = __ldg(S + (size_t)p * N + tid);
-                    const double S2 = __ldg(S + (size_t)(p + half) * N + (N - 1 - tid));
-                    const double qq[2] = {(double)q1, (double)q2}, ss[2] = {S1, S2};
-#pragma unroll
-                    for (int e = 0; e < 2; ++e) {
-                        double term;
-                        if (ss[e] > 0.0) term = qq[e] > 0.0 ? ss[e] * log(qq[e]) - qq[e] : -INFINITY;
-                        else term = -qq[e];
-                        if (a.include_lgamma) term -= lgamma(ss[e] + 1.0);
-                        lacc += term;
-                    }
-                }
-                __syncthreads();
-            }
-            // deterministic block reduction (threads >= N hold 0)
             for (int off = 16; off > 0; off >>= 1) lacc += __shfl_down_sync(0xffffffffu, lacc, off);
             if ((tid & 31) == 0) dred[tid >> 5] = lacc;
             __syncthreads();
@@ -291,7 +378,7 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<N>()) mlem_fused_kernel(F
 }
 
 // ---------------------------------------------------------------- host side
-template <int N, int NT>
+template <int N, int NT, bool QUAD>
 static int fused_occupancy(int V) {
     constexpr int kDev = 16;
     static int cached[kDev][kMaxViews + 1];  // 0 = not yet computed
@@ -300,13 +387,13 @@ static int fused_occupancy(int V) {
     if (V < 0 || V > kMaxViews) return 0;
     if (dev < kDev && cached[dev][V]) return cached[dev][V];
     size_t smem = fused_smem_bytes<N, NT>(V);
-    if (cudaFuncSetAttribute(mlem_fused_kernel<N, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(mlem_fused_kernel<N, NT, QUAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, mlem_fused_kernel<N, NT>, NT, smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, mlem_fused_kernel<N, NT, QUAD>, NT, smem) !=
         cudaSuccess) {
         cudaGetLastError();
         return 0;
@@ -315,23 +402,41 @@ static int fused_occupancy(int V) {
     return nb;
 }
 
-template <int N, int NT>
-static int fused_launch(const FusedArgs& a, int slots, cudaStream_t st) {
+template <int N, int NT, bool QUAD>
+static int fused_launch_t(const FusedArgs& a, int slots, cudaStream_t st) {
     size_t smem = fused_smem_bytes<N, NT>(a.V);
-    if (cudaFuncSetAttribute(mlem_fused_kernel<N, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(mlem_fused_kernel<N, NT, QUAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
         return launch_status();
-    mlem_fused_kernel<N, NT><<<slots, NT, smem, st>>>(a);
+    mlem_fused_kernel<N, NT, QUAD><<<slots, NT, smem, st>>>(a);
     return launch_status();
+}
+
+// Four views per sample grid when the view count allows it, else two.
+template <int N, int NT>
+static int fused_launch(const FusedArgs& a, int slots, cudaStream_t st) {
+    return (a.V % 4 == 0) ? fused_launch_t<N, NT, true>(a, slots, st)
+                          : fused_launch_t<N, NT, false>(a, slots, st);
 }
 
 // Dispatch on the image side: (N, threads per CTA).
 #define BOAC_FUSED_SIZES(X) X(64, 256) X(96, 768) X(128, 1024)
 
+// Workspace for `slots` CTA slots: the attenuation-exponent tables, then the
+// sensitivity images.  Returns the total bytes; *sens_off the offset of the
+// sensitivity images.
+static size_t fused_slot_layout(const boac_geom* g, int slots, size_t* sens_off = nullptr) {
+    const size_t tab = align256(sizeof(float) * (size_t)slots * fused_tab_floats(g->n, g->n_views));
+    if (sens_off) *sens_off = tab;
+    return tab + align256(sizeof(float) * (size_t)slots * g->n * g->n);
+}
+
 int fused_slots(const boac_geom* g, int B) {
     int per_sm = 0;
-#define X(NV, TV) \
-    if (g->n == NV) per_sm = fused_occupancy<NV, TV>(g->n_views);
+#define X(NV, TV)                                                                   \
+    if (g->n == NV)                                                                 \
+        per_sm = (g->n_views % 4 == 0) ? fused_occupancy<NV, TV, true>(g->n_views) \
+                                       : fused_occupancy<NV, TV, false>(g->n_views);
     BOAC_FUSED_SIZES(X)
 #undef X
     if (per_sm <= 0) return 0;
@@ -342,9 +447,7 @@ int fused_slots(const boac_geom* g, int B) {
 size_t fused_workspace_bytes(const boac_geom* g, int B) {
     int slots = fused_slots(g, B);
     if (slots <= 0) return 0;
-    size_t nn = (size_t)g->n * g->n;
-    return align256(sizeof(float) * (size_t)slots * nn * g->n_views) +
-           align256(sizeof(float) * (size_t)slots * nn);
+    return fused_slot_layout(g, slots);
 }
 
 }  // namespace boac
@@ -365,7 +468,6 @@ extern "C" int boac_mlem(const boac_geom* g, const float* mu, const float* S, lo
     if (slots <= 0) return BOAC_ECUDA;
     size_t need = fused_workspace_bytes(g, B);
     if (!ws || ws_bytes < need) return BOAC_EWORKSPACE;
-    size_t nn = (size_t)g->n * g->n;
     FusedArgs a;
     a.mu = mu;
     a.S = S;
@@ -377,9 +479,10 @@ extern "C" int boac_mlem(const boac_geom* g, const float* mu, const float* S, lo
     a.V = g->n_views;
     a.K = K;
     a.dx = g->pixel_cm;
+    size_t sens_off = 0;
+    fused_slot_layout(g, slots, &sens_off);
     a.tab = static_cast<float*>(ws);
-    a.sens = reinterpret_cast<float*>(static_cast<char*>(ws) +
-                                      align256(sizeof(float) * (size_t)slots * nn * g->n_views));
+    a.sens = reinterpret_cast<float*>(static_cast<char*>(ws) + sens_off);
     cudaStream_t st = as_stream(stream);
 #define X(NV, TV) \
     if (g->n == NV) return fused_launch<NV, TV>(a, slots, st);
@@ -432,11 +535,7 @@ static void* noalloc_scratch_ptr() {
 // fit the built-in scratch (0 if not even one does).
 static int noalloc_slots(const boac_geom* g, int B) {
     int slots = fused_slots(g, B);
-    const size_t nn = (size_t)g->n * g->n;
-    while (slots > 0 && align256(sizeof(float) * (size_t)slots * nn * g->n_views) +
-                                align256(sizeof(float) * (size_t)slots * nn) >
-                            kNoAllocScratchBytes)
-        --slots;
+    while (slots > 0 && fused_slot_layout(g, slots) > kNoAllocScratchBytes) --slots;
     return slots;
 }
 
@@ -457,7 +556,6 @@ extern "C" int boac_mlem_noalloc(const boac_geom* g, const float* mu, const floa
     if (slots <= 0) return BOAC_EWORKSPACE;  // one candidate's scratch exceeds 64 MiB
     void* scratch = noalloc_scratch_ptr();
     if (!scratch) return BOAC_ECUDA;
-    const size_t nn = (size_t)g->n * g->n;
     FusedArgs a;
     a.mu = mu;
     a.S = S;
@@ -471,9 +569,10 @@ extern "C" int boac_mlem_noalloc(const boac_geom* g, const float* mu, const floa
     a.dx = g->pixel_cm;
     // The kernel writes every table entry and sensitivity pixel of a slot
     // before reading it, so the scratch needs no clearing between calls.
+    size_t sens_off = 0;
+    fused_slot_layout(g, slots, &sens_off);
     a.tab = static_cast<float*>(scratch);
-    a.sens = reinterpret_cast<float*>(static_cast<char*>(scratch) +
-                                      align256(sizeof(float) * (size_t)slots * nn * g->n_views));
+    a.sens = reinterpret_cast<float*>(static_cast<char*>(scratch) + sens_off);
     cudaStream_t st = as_stream(stream);
 #define X(NV, TV) \
     if (g->n == NV) return fused_launch<NV, TV>(a, slots, st);
