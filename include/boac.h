@@ -181,6 +181,26 @@ int boac_score(const boac_geom *g, const float *mu, const float *S,
                long long s_stride, const float *F, int B, int include_lgamma,
                double *L, void *ws, size_t ws_bytes, void *stream);
 
+/* ---- d ln P / d c: gradient of the score through K MLEM iterations ------
+ * The paper's optimiser is gradient-free (Sec. III); this gives it exact
+ * gradients of the Eq. 5 score with respect to the Legendre coefficients of
+ * Eq. 3, through the AREA rasterisation of Eq. 4 and K unrolled MLEM
+ * iterations from F^0 = 1 (reverse mode; F^n is recomputed from checkpoints
+ * stored every ckpt_every iterations, which changes memory, not results).
+ *   t, c    tissue values and [B][6] float32 coefficients (device)
+ *   S       sinogram(s) as for boac_mlem
+ *   L       [B] float64 score, dL_dc [B][6] float64 gradient (device outputs)
+ *   F_out   [B][n][n] F^K, or NULL
+ *   ws      boac_score_grad_workspace_bytes(g, B, K, ckpt_every) bytes
+ * Float32 arithmetic except the score and the final sum over pixels
+ * (float64).  Where q = 0 < S (L = -inf) the gradient is taken as 0 there. */
+size_t boac_score_grad_workspace_bytes(const boac_geom *g, int B, int K,
+                                       int ckpt_every);
+int boac_score_grad(const boac_geom *g, const boac_tissue *t, const float *c,
+                    const float *S, long long s_stride, int K, int ckpt_every,
+                    int B, int include_lgamma, double *L, double *dL_dc,
+                    float *F_out, void *ws, size_t ws_bytes, void *stream);
+
 /* Eq. 5 reduction alone, for expected counts q already on the device:
  *   q [B][n_views][n_bins] float32, S as above, L [B] float64 output. */
 int boac_loglik(const boac_geom *g, const float *q, const float *S,

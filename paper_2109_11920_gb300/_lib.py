@@ -79,6 +79,8 @@ SIGNATURES = {
     "boac_mlem_noalloc": (_I, [_GP, _P, _P, _LL, _P, _I, _I, _P, _I, _P]),
     "boac_score": (_I, [_GP, _P, _P, _LL, _P, _I, _I, _P, _P, _SZ, _P]),
     "boac_loglik": (_I, [_GP, _P, _P, _LL, _I, _I, _P, _P]),
+    "boac_score_grad_workspace_bytes": (_SZ, [_GP, _I, _I, _I]),
+    "boac_score_grad": (_I, [_GP, _TP, _P, _P, _LL, _I, _I, _I, _I, _P, _P, _P, _P, _SZ, _P]),
 }
 
 

@@ -159,3 +159,48 @@ def boac_loglik(g: Geom, q: torch.Tensor, S: torch.Tensor, include_lgamma: bool 
     check("boac_loglik", _lib.load().boac_loglik(
         ctypes.byref(g), _ptr(q), _ptr(S), stride, B, int(include_lgamma), _ptr(L), _stream(q.device)))
     return L
+
+
+def boac_score_grad(g: Geom, t: Tissue, c: torch.Tensor, S: torch.Tensor, K: int,
+                    ckpt_every: int = 2, include_lgamma: bool = True, want_image: bool = False,
+                    ws: torch.Tensor | None = None):
+    """Score after K MLEM iterations (AREA map, F^0 = 1) and its gradient with
+    respect to the Legendre coefficients: returns (L[B], dL/dc[B, 6], F^K or None),
+    L and dL/dc in float64."""
+    _need(c, "c", torch.float32)
+    if c.dim() != 2 or c.shape[1] != 6:
+        raise ValueError("c must be [B, 6]")
+    B = c.shape[0]
+    S, stride = _sino(S, g, B)
+    lib = _lib.load()
+    if ws is None:
+        nbytes = int(lib.boac_score_grad_workspace_bytes(ctypes.byref(g), B, int(K), int(ckpt_every)))
+        if nbytes == 0:
+            raise ValueError("invalid arguments for boac_score_grad")
+        ws = torch.empty(nbytes, dtype=torch.uint8, device=c.device)
+    L = torch.empty(B, dtype=torch.float64, device=c.device)
+    grad = torch.empty(B, 6, dtype=torch.float64, device=c.device)
+    F = torch.empty(B, g.n, g.n, dtype=torch.float32, device=c.device) if want_image else None
+    check("boac_score_grad", lib.boac_score_grad(
+        ctypes.byref(g), ctypes.byref(t), _ptr(c), _ptr(S), stride, int(K), int(ckpt_every), B,
+        int(include_lgamma), _ptr(L), _ptr(grad), _ptr(F), _ptr(ws), ws.numel(), _stream(c.device)))
+    return L, grad, F
+
+
+class BoacScore(torch.autograd.Function):
+    """ln P(S | F^K(c), A^mu(c)) as a differentiable function of the Legendre
+    coefficients c[B, 6]: the forward runs boac_score_grad (which returns the
+    gradient together with the score), the backward scales it by the incoming
+    gradient.  Usage: ``L = BoacScore.apply(c, geom, tissue, S, K, ckpt_every)``."""
+
+    @staticmethod
+    def forward(ctx, c, g, t, S, K, ckpt_every=2, include_lgamma=True):
+        L, grad, _ = boac_score_grad(g, t, c.detach().contiguous(), S, K, ckpt_every, include_lgamma)
+        ctx.save_for_backward(grad)
+        ctx.c_dtype = c.dtype
+        return L
+
+    @staticmethod
+    def backward(ctx, gL):
+        (grad,) = ctx.saved_tensors
+        return (gL[:, None] * grad).to(ctx.c_dtype), None, None, None, None, None, None

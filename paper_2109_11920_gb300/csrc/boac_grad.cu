@@ -1,0 +1,346 @@
+// boac_grad.cu -- d ln P / d c_k: the derivative of the Eq. 5 score after K
+// MLEM iterations (Sec. III step 3) with respect to the Legendre coefficients
+// of Eq. 3, through the AREA rasterisation of Eq. 4.  The paper's optimiser
+// is gradient-free; this gives the Bayesian optimiser gradients it can use
+// alongside its surrogate.
+//
+// Exact reverse mode of the discretised pipeline, batched over candidates:
+//   forward:  mu = raster(c); a = attenuation table; sens = A^T 1;
+//             F^{n+1} = F^n (A^T (S / A F^n)) / sens, F^0 = 1;
+//             L = sum S ln q - q [- ln S!], q = A F^K
+//   reverse:  qbar = S/q - 1;  Fbar = A^T qbar;  abar += dx qbar (B F^K)
+//             for n = K-1 .. 0 (F^n recomputed segment by segment from
+//             checkpoints stored every `ckpt_every` iterations):
+//               zbar = Fbar F^n / sens;  sensbar -= Fbar F^{n+1} / sens;
+//               Fbar <- Fbar z^n / sens + A^T qbar',
+//               with rbar = A zbar, qbar' = -rbar S / q^2,
+//               abar += dx (r^n (B zbar) + qbar' (B F^n))
+//             abar += dx (B sensbar)                       (sens = A^T 1)
+//             mbar_k = -dx (abar_k a_k / 2 + sum_{k'<k} abar_k' a_k')
+//             mubar = sum_v B_v^T mbar_v
+//             dL/dc_k = sum_pixels mubar dmu/dR P_k(cos theta)   (float64)
+// where B_v is bilinear sampling on view v's ray grid and abar the adjoint of
+// the attenuation factor of every ray sample.  Float32 throughout except the
+// score and the final sum over pixels, which are float64.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "boac_device.cuh"
+#include "boac_internal.h"
+#include "boac_plain_kernels.cuh"
+
+namespace boac {
+
+// abar[cand][v][k][b] += dx (y1[v][b] (B_v X1)(k, b) + y2[v][b] (B_v X2)(k, b))
+// (y == nullptr: 1; X2 == nullptr: no second term).  One thread per ray.
+__global__ void abar_accum_kernel(int n, int V, float dx, const float* __restrict__ y1,
+                                  const float* __restrict__ X1, const float* __restrict__ y2,
+                                  const float* __restrict__ X2, float* __restrict__ abar) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x, v = blockIdx.y, cand = blockIdx.z;
+    if (b >= n) return;
+    const size_t nn = (size_t)n * n, vb = (size_t)V * n;
+    const float w1 = dx * (y1 ? __ldg(y1 + cand * vb + (size_t)v * n + b) : 1.0f);
+    const float w2 = X2 ? dx * (y2 ? __ldg(y2 + cand * vb + (size_t)v * n + b) : 1.0f) : 0.0f;
+    if (w1 == 0.0f && w2 == 0.0f) return;
+    const float* x1 = X1 + cand * nn;
+    const float* x2 = X2 ? X2 + cand * nn : nullptr;
+    float* ab = abar + ((size_t)cand * V + v) * nn;
+    float cs, sn;
+    view_cos_sin(v, V, &cs, &sn);
+    const float c = 0.5f * (float)(n - 1);
+    for (int k = 0; k < n; ++k) {
+        float u, w;
+        sample_uw(k, b, cs, sn, c, &u, &w);
+        float add = w1 * bilerp_global(x1, n, u, w);
+        if (x2) add = fmaf(w2, bilerp_global(x2, n, u, w), add);
+        ab[(size_t)k * n + b] += add;
+    }
+}
+
+// In place: abar -> mbar_k = -dx (abar_k a_k / 2 + sum_{k' < k} abar_k' a_k')
+// (derivative of a_k = exp(-dx (m_k/2 + sum_{k'>k} m_k')) w.r.t. the mu
+// samples m of the ray).  One thread per ray.
+__global__ void mbar_kernel(int n, int V, float dx, const float* __restrict__ tab,
+                            float* __restrict__ abar) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x, v = blockIdx.y, cand = blockIdx.z;
+    if (b >= n) return;
+    const size_t nn = (size_t)n * n;
+    const float* t = tab + ((size_t)cand * V + v) * nn;
+    float* ab = abar + ((size_t)cand * V + v) * nn;
+    float prefix = 0.0f;
+    for (int k = 0; k < n; ++k) {
+        const float aa = ab[(size_t)k * n + b] * __ldg(t + (size_t)k * n + b);
+        ab[(size_t)k * n + b] = -dx * (0.5f * aa + prefix);
+        prefix += aa;
+    }
+}
+
+__global__ void fill_ones_kernel(long long count, float* __restrict__ x) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+         i += (long long)gridDim.x * blockDim.x)
+        x[i] = 1.0f;
+}
+
+// r = S / q over B candidates (0 where q <= 0); S rows s_stride apart.
+__global__ void ratio_batched_kernel(int B, int nbin, const float* __restrict__ S, long long s_stride,
+                                     const float* __restrict__ q, float* __restrict__ r) {
+    const long long total = (long long)B * nbin;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int cand = (int)(i / nbin), j = (int)(i % nbin);
+        const float qi = q[i];
+        r[i] = qi > 0.0f ? __ldg(S + cand * s_stride + j) / qi : 0.0f;
+    }
+}
+
+// d L / d q^K: S/q - 1 (S > 0, q > 0), -1 (S == 0), 0 where L = -inf.
+__global__ void qbar_final_kernel(int B, int nbin, const float* __restrict__ S, long long s_stride,
+                                  const float* __restrict__ q, float* __restrict__ qbar) {
+    const long long total = (long long)B * nbin;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int cand = (int)(i / nbin), j = (int)(i % nbin);
+        const float s = __ldg(S + cand * s_stride + j), qi = q[i];
+        qbar[i] = s > 0.0f ? (qi > 0.0f ? s / qi - 1.0f : 0.0f) : -1.0f;
+    }
+}
+
+// qbar = -rbar S / q^2 where q > 0 (r = S / q), else 0.
+__global__ void qbar_step_kernel(int B, int nbin, const float* __restrict__ S, long long s_stride,
+                                 const float* __restrict__ q, const float* __restrict__ rbar,
+                                 float* __restrict__ qbar) {
+    const long long total = (long long)B * nbin;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int cand = (int)(i / nbin), j = (int)(i % nbin);
+        const float qi = q[i];
+        qbar[i] = qi > 0.0f ? -rbar[i] * (__ldg(S + cand * s_stride + j) / (qi * qi)) : 0.0f;
+    }
+}
+
+// Adjoint of F^{n+1} = F^n z / sens for one step (per pixel):
+//   zbar = Fbar F^n / sens; sensbar -= Fbar F^{n+1} / sens; Fnew = Fbar z / sens.
+__global__ void mlem_step_adjoint_kernel(long long count, const float* __restrict__ Fbar,
+                                         const float* __restrict__ Fn, const float* __restrict__ Fn1,
+                                         const float* __restrict__ z, const float* __restrict__ sens,
+                                         float* __restrict__ zbar, float* __restrict__ sensbar,
+                                         float* __restrict__ Fnew) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float s = sens[i];
+        if (s > 0.0f) {
+            const float fb = Fbar[i] / s;
+            zbar[i] = fb * Fn[i];
+            sensbar[i] -= fb * Fn1[i];
+            Fnew[i] = fb * z[i];
+        } else {
+            zbar[i] = 0.0f;
+            Fnew[i] = 0.0f;
+        }
+    }
+}
+
+// dL/dc_k = sum_pixels mubar dmu/dR P_k(z) for the AREA map
+//   mu = (mu_b - mu_c) f(R) + mu_c f(R + dR), f(R') = clamp(1/2 + (R'-r)/dx, 0, 1),
+//   R = max(0, sum c_k P_k(z)):  dmu/dR = ((mu_b - mu_c) f'(R) + mu_c f'(R+dR)) [R > 0],
+// accumulated in float64 with a fixed reduction tree.  One block per candidate.
+__global__ void grad_coef_kernel(int n, double dx, double mu_b, double mu_c, double dR,
+                                 const float* __restrict__ coef, const float* __restrict__ mubar,
+                                 double* __restrict__ grad) {
+    __shared__ double part[32][6];
+    const int cand = blockIdx.x;
+    double c6[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) c6[k] = (double)__ldg(coef + cand * 6 + k);
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    const double cc = 0.5 * (double)(n - 1);
+    const float* mb = mubar + (size_t)cand * n * n;
+    for (int pix = threadIdx.x; pix < n * n; pix += blockDim.x) {
+        const int i = pix / n, j = pix % n;
+        const double x = ((double)j - cc) * dx, y = ((double)i - cc) * dx;
+        const double r = sqrt(x * x + y * y);
+        const double z = r > 0.0 ? x / r : 1.0;
+        double P[6];
+        P[0] = 1.0;
+        P[1] = z;
+#pragma unroll
+        for (int k = 1; k < 5; ++k) P[k + 1] = ((2 * k + 1) * z * P[k] - k * P[k - 1]) / (k + 1);
+        double R = 0.0;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) R += c6[k] * P[k];
+        if (!(R > 0.0)) continue;
+        const double ein = 0.5 + (R - r) / dx, eout = 0.5 + (R + dR - r) / dx;
+        const double din = (ein > 0.0 && ein < 1.0) ? 1.0 / dx : 0.0;
+        const double dout = (eout > 0.0 && eout < 1.0) ? 1.0 / dx : 0.0;
+        const double dmu = (mu_b - mu_c) * din + mu_c * dout;
+        if (dmu == 0.0) continue;
+        const double s = (double)mb[pix] * dmu;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) acc[k] += s * P[k];
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+        for (int off = 16; off > 0; off >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], off);
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) part[threadIdx.x >> 5][k] = acc[k];
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w][threadIdx.x];
+        grad[cand * 6 + threadIdx.x] = t;
+    }
+}
+
+// ------------------------------------------------------------- workspace
+struct GradLayout {
+    size_t mu, tab, abar, sens, sensbar, Fbar, Fnew, zbar, mubar, Fk, ck, Fseg, zseg, qseg, rseg, qK,
+        qbar, rbar, total;
+};
+
+static GradLayout grad_layout(const boac_geom* g, int B, int K, int ckpt) {
+    const size_t nn = (size_t)g->n * g->n, vb = (size_t)g->n_views * g->n_bins;
+    const size_t Bs = (size_t)B;
+    const int nseg = (K + ckpt - 1) / ckpt;
+    GradLayout L{};
+    size_t off = 0;
+    auto take = [&](size_t floats) {
+        size_t o = off;
+        off += align256(floats * sizeof(float));
+        return o;
+    };
+    L.mu = take(Bs * nn);
+    L.tab = take(Bs * g->n_views * nn);
+    L.abar = take(Bs * g->n_views * nn);
+    L.sens = take(Bs * nn);
+    L.sensbar = take(Bs * nn);
+    L.Fbar = take(Bs * nn);
+    L.Fnew = take(Bs * nn);
+    L.zbar = take(Bs * nn);
+    L.mubar = take(Bs * nn);
+    L.Fk = take(Bs * nn);
+    L.ck = take(Bs * (size_t)(nseg > 0 ? nseg : 1) * nn);
+    L.Fseg = take(Bs * (size_t)(ckpt + 1) * nn);
+    L.zseg = take(Bs * (size_t)ckpt * nn);
+    L.qseg = take(Bs * (size_t)ckpt * vb);
+    L.rseg = take(Bs * (size_t)ckpt * vb);
+    L.qK = take(Bs * vb);
+    L.qbar = take(Bs * vb);
+    L.rbar = take(Bs * vb);
+    L.total = off;
+    return L;
+}
+
+}  // namespace boac
+
+using namespace boac;
+
+extern "C" size_t boac_score_grad_workspace_bytes(const boac_geom* g, int B, int K, int ckpt_every) {
+    if (!geom_ok(g) || B < 1 || B > 65535 || K < 0 || ckpt_every < 1) return 0;
+    return grad_layout(g, B, K, ckpt_every).total;
+}
+
+extern "C" int boac_score_grad(const boac_geom* g, const boac_tissue* t, const float* c,
+                               const float* S, long long s_stride, int K, int ckpt_every, int B,
+                               int include_lgamma, double* L, double* dL_dc, float* F_out, void* ws,
+                               size_t ws_bytes, void* stream) {
+    if (!geom_ok(g) || !t || !c || !S || !L || !dL_dc || B < 1 || B > 65535 || K < 0 ||
+        ckpt_every < 1 || s_stride < 0)
+        return BOAC_EINVAL;
+    const GradLayout lay = grad_layout(g, B, K, ckpt_every);
+    if (!ws || ws_bytes < lay.total) return BOAC_EWORKSPACE;
+    char* base = static_cast<char*>(ws);
+    auto P = [&](size_t off) { return reinterpret_cast<float*>(base + off); };
+    float *mu = P(lay.mu), *tab = P(lay.tab), *abar = P(lay.abar), *sens = P(lay.sens),
+          *sensbar = P(lay.sensbar), *Fbar = P(lay.Fbar), *Fnew = P(lay.Fnew), *zbar = P(lay.zbar),
+          *mubar = P(lay.mubar), *Fk = P(lay.Fk), *ck = P(lay.ck), *Fseg = P(lay.Fseg),
+          *zseg = P(lay.zseg), *qseg = P(lay.qseg), *rseg = P(lay.rseg), *qK = P(lay.qK),
+          *qbar = P(lay.qbar), *rbar = P(lay.rbar);
+    cudaStream_t st = as_stream(stream);
+    const int n = g->n, V = g->n_views;
+    const float dx = g->pixel_cm;
+    const size_t nn = (size_t)n * n, vb = (size_t)V * g->n_bins;
+    const long long cnt_pix = (long long)B * nn, cnt_bin = (long long)B * vb;
+    const dim3 rg = ray_grid(g, B);
+    const dim3 pg((unsigned)((nn + kPixThreads - 1) / kPixThreads), B);
+    const size_t smem = sizeof(float) * 2 * V;
+    const int g1p = grid_1d(cnt_pix, 256), g1b = grid_1d(cnt_bin, 256);
+
+    // one MLEM step F_in -> F_out, leaving q, r and z = A^T r behind
+    auto mlem_step = [&](const float* F_in, float* F_o, float* q, float* r, float* z) {
+        project_table_kernel<<<rg, kRayThreads, 0, st>>>(n, V, dx, tab, F_in, q);
+        ratio_batched_kernel<<<g1b, 256, 0, st>>>(B, (int)vb, S, s_stride, q, r);
+        backproject_gather_kernel<<<pg, kPixThreads, smem, st>>>(n, V, dx, tab, r, z, 0);
+        cudaMemcpyAsync(F_o, F_in, sizeof(float) * cnt_pix, cudaMemcpyDeviceToDevice, st);
+        update_kernel<<<g1p, 256, 0, st>>>((int)cnt_pix, F_o, z, sens);
+    };
+    // ---- forward
+    int s = boac_rasterize_mu(g, t, c, B, BOAC_RASTER_AREA, mu, stream);
+    if (s != BOAC_OK) return s;
+    attenuation_table_kernel<<<rg, kRayThreads, 0, st>>>(n, V, dx, mu, tab);
+    backproject_gather_kernel<<<pg, kPixThreads, smem, st>>>(n, V, dx, tab, nullptr, sens, 0);
+    cudaMemsetAsync(abar, 0, sizeof(float) * (size_t)B * V * nn, st);
+    cudaMemsetAsync(sensbar, 0, sizeof(float) * cnt_pix, st);
+    // F^0 = 1 into checkpoint 0; F^{j ckpt} into checkpoint j; F^K into Fk.
+    // Iterates in between alternate between two temporaries (Fbar and Fnew
+    // are not yet in use).
+    fill_ones_kernel<<<g1p, 256, 0, st>>>(cnt_pix, ck);
+    {
+        const float* cur = ck;
+        float* temps[2] = {Fnew, Fbar};
+        int next_temp = 0;
+        for (int it = 0; it < K; ++it) {
+            float* nxt;
+            if (it + 1 == K) nxt = Fk;
+            else if ((it + 1) % ckpt_every == 0) nxt = ck + (size_t)((it + 1) / ckpt_every) * B * nn;
+            else {
+                nxt = temps[next_temp];
+                next_temp ^= 1;
+            }
+            mlem_step(cur, nxt, qseg, rseg, zseg);
+            cur = nxt;
+        }
+        if (K == 0) cudaMemcpyAsync(Fk, ck, sizeof(float) * cnt_pix, cudaMemcpyDeviceToDevice, st);
+    }
+    // ---- score and d L / d q^K
+    project_table_kernel<<<rg, kRayThreads, 0, st>>>(n, V, dx, tab, Fk, qK);
+    loglik_kernel<<<B, 256, 0, st>>>((int)vb, qK, S, s_stride, include_lgamma, L);
+    if (F_out) cudaMemcpyAsync(F_out, Fk, sizeof(float) * cnt_pix, cudaMemcpyDeviceToDevice, st);
+    qbar_final_kernel<<<g1b, 256, 0, st>>>(B, (int)vb, S, s_stride, qK, qbar);
+    backproject_gather_kernel<<<pg, kPixThreads, smem, st>>>(n, V, dx, tab, qbar, Fbar, 0);
+    abar_accum_kernel<<<rg, kRayThreads, 0, st>>>(n, V, dx, qbar, Fk, nullptr, nullptr, abar);
+
+    // ---- reverse through the iterations, one checkpoint segment at a time
+    const int nseg = (K + ckpt_every - 1) / ckpt_every;
+    for (int j = nseg - 1; j >= 0; --j) {
+        const int n0 = j * ckpt_every;
+        const int len = (K - n0) < ckpt_every ? (K - n0) : ckpt_every;
+        cudaMemcpyAsync(Fseg, ck + (size_t)j * B * nn, sizeof(float) * cnt_pix, cudaMemcpyDeviceToDevice, st);
+        for (int tt = 0; tt < len; ++tt)
+            mlem_step(Fseg + (size_t)tt * B * nn, Fseg + (size_t)(tt + 1) * B * nn, qseg + (size_t)tt * B * vb,
+                      rseg + (size_t)tt * B * vb, zseg + (size_t)tt * B * nn);
+        for (int tt = len - 1; tt >= 0; --tt) {
+            const float* Fn = Fseg + (size_t)tt * B * nn;
+            const float* Fn1 = Fseg + (size_t)(tt + 1) * B * nn;
+            const float* q = qseg + (size_t)tt * B * vb;
+            const float* r = rseg + (size_t)tt * B * vb;
+            const float* z = zseg + (size_t)tt * B * nn;
+            mlem_step_adjoint_kernel<<<g1p, 256, 0, st>>>(cnt_pix, Fbar, Fn, Fn1, z, sens, zbar, sensbar, Fnew);
+            project_table_kernel<<<rg, kRayThreads, 0, st>>>(n, V, dx, tab, zbar, rbar);
+            qbar_step_kernel<<<g1b, 256, 0, st>>>(B, (int)vb, S, s_stride, q, rbar, qbar);
+            backproject_gather_kernel<<<pg, kPixThreads, smem, st>>>(n, V, dx, tab, qbar, Fnew, 1);
+            abar_accum_kernel<<<rg, kRayThreads, 0, st>>>(n, V, dx, r, zbar, qbar, Fn, abar);
+            float* tmp = Fbar;
+            Fbar = Fnew;
+            Fnew = tmp;
+        }
+    }
+    // sens = A^T 1
+    abar_accum_kernel<<<rg, kRayThreads, 0, st>>>(n, V, dx, nullptr, sensbar, nullptr, nullptr, abar);
+    // attenuation -> mu samples -> pixels -> coefficients
+    mbar_kernel<<<rg, kRayThreads, 0, st>>>(n, V, dx, tab, abar);
+    backproject_gather_kernel<<<pg, kPixThreads, smem, st>>>(n, V, 1.0f, abar, nullptr, mubar, 0);
+    grad_coef_kernel<<<B, 256, 0, st>>>(n, (double)dx, (double)t->mu_b, (double)t->mu_c, (double)t->dR, c,
+                                        mubar, dL_dc);
+    return launch_status();
+}

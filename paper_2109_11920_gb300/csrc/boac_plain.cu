@@ -14,11 +14,9 @@
 
 #include "boac_device.cuh"
 #include "boac_internal.h"
+#include "boac_plain_kernels.cuh"
 
 namespace boac {
-
-constexpr int kRayThreads = 128;
-constexpr int kPixThreads = 256;
 
 // attenuation factor of every ray sample: tab[cand][v][k][b]
 __global__ void attenuation_table_kernel(int n, int V, float dx, const float* __restrict__ mu,
@@ -84,9 +82,11 @@ __global__ void project_table_kernel(int n, int V, float dx, const float* __rest
     q[((size_t)cand * V + v) * n + b] = dx * acc;
 }
 
-// out[cand] = A^T y[cand] (y == nullptr: y = 1), as a per-pixel gather.
-__global__ void backproject_gather_kernel(int n, int V, float dx, const float* __restrict__ tab,
-                                          const float* __restrict__ y, float* __restrict__ out) {
+// out[cand] (+)= scale * sum_v B_v^T (tab_v * y_v) (y == nullptr: y = 1), as
+// a per-pixel gather: with tab = attenuation and scale = dx this is A^T y.
+__global__ void backproject_gather_kernel(int n, int V, float scale, const float* __restrict__ tab,
+                                          const float* __restrict__ y, float* __restrict__ out,
+                                          int accumulate) {
     extern __shared__ float csn[];  // [V][2]
     for (int v = threadIdx.x; v < V; v += blockDim.x) view_cos_sin(v, V, &csn[2 * v], &csn[2 * v + 1]);
     __syncthreads();
@@ -124,7 +124,8 @@ __global__ void backproject_gather_kernel(int n, int V, float dx, const float* _
         }
         acc += vacc;
     }
-    out[(size_t)cand * nn + pix] = dx * acc;
+    float* o = out + (size_t)cand * nn + pix;
+    *o = accumulate ? *o + scale * acc : scale * acc;
 }
 
 __global__ void ratio_kernel(int count, const float* __restrict__ S, const float* __restrict__ q,
@@ -170,11 +171,11 @@ __global__ void loglik_kernel(int nbin, const float* __restrict__ q, const float
     }
 }
 
-static dim3 ray_grid(const boac_geom* g, int B) {
+dim3 ray_grid(const boac_geom* g, int B) {
     return dim3((g->n + kRayThreads - 1) / kRayThreads, g->n_views, B);
 }
 
-static int grid_1d(long long count, int threads) {
+int grid_1d(long long count, int threads) {
     long long b = (count + threads - 1) / threads;
     long long cap = 16LL * (sm_count() > 0 ? sm_count() : 1);
     return (int)(b < cap ? b : cap);
@@ -209,7 +210,7 @@ extern "C" int boac_backproject(const boac_geom* g, const float* mu, const float
         dim3 grid((unsigned)((nn + kPixThreads - 1) / kPixThreads), cb);
         backproject_gather_kernel<<<grid, kPixThreads, smem, st>>>(
             g->n, g->n_views, g->pixel_cm, tab,
-            y ? y + (size_t)c0 * g->n_views * g->n_bins : nullptr, out + c0 * nn);
+            y ? y + (size_t)c0 * g->n_views * g->n_bins : nullptr, out + c0 * nn, 0);
         int s = launch_status();
         if (s != BOAC_OK) return s;
     }
@@ -263,11 +264,11 @@ extern "C" int boac_mlem_plain(const boac_geom* g, const float* mu, const float*
         const float* S_c = S + (size_t)cand * s_stride;
         float* F_c = F + cand * nn;
         attenuation_table_kernel<<<ray_grid(g, 1), kRayThreads, 0, st>>>(n, V, dx, m_c, tab);
-        backproject_gather_kernel<<<pgrid, kPixThreads, smem, st>>>(n, V, dx, tab, nullptr, sens);
+        backproject_gather_kernel<<<pgrid, kPixThreads, smem, st>>>(n, V, dx, tab, nullptr, sens, 0);
         for (int it = 0; it < K; ++it) {
             project_table_kernel<<<ray_grid(g, 1), kRayThreads, 0, st>>>(n, V, dx, tab, F_c, q);
             ratio_kernel<<<grid_1d((long long)vb, 256), 256, 0, st>>>((int)vb, S_c, q, r);
-            backproject_gather_kernel<<<pgrid, kPixThreads, smem, st>>>(n, V, dx, tab, r, bp);
+            backproject_gather_kernel<<<pgrid, kPixThreads, smem, st>>>(n, V, dx, tab, r, bp, 0);
             update_kernel<<<grid_1d((long long)nn, 256), 256, 0, st>>>((int)nn, F_c, bp, sens);
         }
         if (L) {

@@ -1,0 +1,34 @@
+// boac_plain_kernels.cuh -- the unfused kernels of boac_plain.cu, declared
+// for reuse by the gradient path (boac_grad.cu).  All are batched over
+// candidates (grid z or y) and documented at their definitions.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "boac_internal.h"
+
+namespace boac {
+
+constexpr int kRayThreads = 128;   // ray kernels: one thread per (candidate, view, bin)
+constexpr int kPixThreads = 256;   // pixel kernels: one thread per (candidate, pixel)
+
+__global__ void attenuation_table_kernel(int n, int V, float dx, const float* __restrict__ mu,
+                                         float* __restrict__ tab);
+__global__ void project_otf_kernel(int n, int V, float dx, const float* __restrict__ mu,
+                                   const float* __restrict__ F, float* __restrict__ q);
+__global__ void project_table_kernel(int n, int V, float dx, const float* __restrict__ tab,
+                                     const float* __restrict__ F, float* __restrict__ q);
+__global__ void backproject_gather_kernel(int n, int V, float scale, const float* __restrict__ tab,
+                                          const float* __restrict__ y, float* __restrict__ out,
+                                          int accumulate);
+__global__ void ratio_kernel(int count, const float* __restrict__ S, const float* __restrict__ q,
+                             float* __restrict__ r);
+__global__ void update_kernel(int count, float* __restrict__ F, const float* __restrict__ bp,
+                              const float* __restrict__ sens);
+__global__ void loglik_kernel(int nbin, const float* __restrict__ q, const float* __restrict__ S,
+                              long long s_stride, int include_lgamma, double* __restrict__ L);
+
+dim3 ray_grid(const boac_geom* g, int B);
+int grid_1d(long long count, int threads);
+
+}  // namespace boac
