@@ -37,12 +37,13 @@ __device__ __forceinline__ void view_cos_sin(int v, int V, float* cs, float* sn)
 // Continuous (column u, row w) pixel index of ray sample k of bin b in the
 // view with (cs, sn): p = s (cs, sn) + t (-sn, cs), s = (b - c) dx,
 // t = (k - c) dx, c = (n - 1) / 2 (bins and samples share the pixel pitch).
+// The bin term is innermost so that loops along a ray can hoist it.
 __device__ __forceinline__ void sample_uw(int k, int b, float cs, float sn, float c,
                                           float* u, float* w) {
     float bc = (float)b - c;
     float kc = (float)k - c;
-    *u = fmaf(bc, cs, fmaf(-kc, sn, c));
-    *w = fmaf(bc, sn, fmaf(kc, cs, c));
+    *u = fmaf(-kc, sn, fmaf(bc, cs, c));
+    *w = fmaf(kc, cs, fmaf(bc, sn, c));
 }
 
 __device__ __forceinline__ bool inside_open(float u, float w, int n) {

@@ -4,7 +4,7 @@
 // last paragraph).
 //
 // One CTA owns one candidate at a time and keeps its whole state on chip:
-//   img0  F (padded n+2 rows x n+3 floats, zero ring)   -- mu during set-up
+//   img0  F (padded n+2 rows x n+1 floats, zero ring)   -- mu during set-up
 //   img1  back-projection accumulator (same layout)
 //   W     n x (n+1) ray-sample buffer (F samples, then G = dx a r)
 // The candidate's "system matrix" -- the attenuation of every ray sample --
@@ -52,8 +52,12 @@ struct FusedArgs {
 // Shared-memory and work layout of one CTA (image side N, NT threads).
 template <int N, int NT>
 struct FusedShape {
-    static constexpr int P = N + 3;          // padded image pitch (odd)
-    static constexpr int IMG = (N + 2) * P;  // floats per padded image
+    // Padded image: pixel (i, j), i, j in [-1, n], at (i+1) P + (j+1) with
+    // P = n + 1, so the right padding column of row i and the left padding
+    // column of row i+1 are the same zero cell; P = 1 (mod 32) for n a
+    // multiple of 32 spreads rotated rows of samples over the banks.
+    static constexpr int P = N + 1;
+    static constexpr int IMG = (N + 1) * (N + 2) + 1;
     static constexpr int NN = N * N;
     static constexpr int WP = N + 1;         // sample-buffer pitch (odd)
     static constexpr int NSEG = NT / N;      // segments per column / row
@@ -105,6 +109,13 @@ __device__ __forceinline__ void scatter_classes(const float* __restrict__ W, flo
         }
         __syncthreads();
     }
+}
+
+// 2^x with the hardware approximation (relative error about 2^-22).
+__device__ __forceinline__ float ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
 
 __device__ __forceinline__ double loglik_term(double s, double q, int include_lgamma) {
@@ -229,7 +240,7 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<N>()) mlem_fused_kernel(F
                 for (int s = 0; s < SEG; ++s) {
                     const int k = k0 + s;
                     const float y = Xc[k * N + lb];
-                    W[k * WP + lb] = dx * (exp2f(y) + exp2f(uc - y));
+                    W[k * WP + lb] = dx * (ex2(y) + ex2(uc - y));
                 }
             }
             if (QUAD) {
@@ -238,7 +249,7 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<N>()) mlem_fused_kernel(F
                 for (int s = 0; s < SEG; ++s) {
                     const int b = k0 + s;
                     const float y = XrT[b * N + lb];
-                    W[lb * WP + b] += dx * (exp2f(y) + exp2f(ur - y));
+                    W[lb * WP + b] += dx * (ex2(y) + ex2(ur - y));
                 }
             }
             __syncthreads();
@@ -277,8 +288,8 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<N>()) mlem_fused_kernel(F
                         const float f = bilerp_padded(img0, P, N, u, w);
                         if (QUAD) W[k * WP + lb] = f;
                         const float y = Xc[k * N + lb];
-                        acc1 = fmaf(exp2f(y), f, acc1);
-                        acc2 = fmaf(exp2f(uc - y), f, acc2);
+                        acc1 = fmaf(ex2(y), f, acc1);
+                        acc2 = fmaf(ex2(uc - y), f, acc2);
                     }
                     redc[seg * N + lb] = acc1;
                     redc[(NSEG + seg) * N + lb] = acc2;
@@ -291,8 +302,8 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<N>()) mlem_fused_kernel(F
                         const int b = k0 + s;
                         const float f = W[lb * WP + b];
                         const float y = XrT[b * N + lb];
-                        acc3 = fmaf(exp2f(y), f, acc3);
-                        acc4 = fmaf(exp2f(ur - y), f, acc4);
+                        acc3 = fmaf(ex2(y), f, acc3);
+                        acc4 = fmaf(ex2(ur - y), f, acc4);
                     }
                     redr[seg * N + lb] = acc3;
                     redr[(NSEG + seg) * N + lb] = acc4;
@@ -330,7 +341,7 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<N>()) mlem_fused_kernel(F
                     for (int s = 0; s < SEG; ++s) {
                         const int k = k0 + s;
                         const float y = Xc[k * N + lb];
-                        W[k * WP + lb] = fmaf(exp2f(y), r1, exp2f(uc - y) * r2);
+                        W[k * WP + lb] = fmaf(ex2(y), r1, ex2(uc - y) * r2);
                     }
                 }
                 if (QUAD) {
@@ -340,7 +351,7 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<N>()) mlem_fused_kernel(F
                     for (int s = 0; s < SEG; ++s) {
                         const int b = k0 + s;
                         const float y = XrT[b * N + lb];
-                        W[lb * WP + b] += fmaf(exp2f(y), r3, exp2f(ur - y) * r4);
+                        W[lb * WP + b] += fmaf(ex2(y), r3, ex2(ur - y) * r4);
                     }
                 }
                 __syncthreads();
