@@ -151,6 +151,52 @@ int boac_mlem_plain(const boac_geom *g, const float *mu, const float *S,
                     int include_lgamma, void *ws, size_t ws_bytes,
                     void *stream);
 
+/* ---- ragged batches -------------------------------------------------------
+ * Candidates of different image sizes and iteration counts in one call
+ * (Sec. III step 3 for every candidate; batching is this library's).  Each
+ * candidate names a size class (a geometry in classes[]), its iteration count
+ * K and the float offsets of its mu [n][n], sinogram [n_views][n] and image
+ * F [n][n] (in: initial image, out: F^K) in three caller-owned device pools.
+ * Its score (Eq. 5, as boac_mlem) goes to L[index in cands].  Per class, one
+ * persistent fused kernel takes candidates from a work queue, largest K
+ * first.  config[c] (host array, or NULL for defaults) picks class c's launch
+ * shape: 2 * shape + pair, shape 0/1/2 = CTAs of 2n/4n/8n (<= 1024) threads,
+ * pair = 1 for two views per sample grid instead of four (four needs
+ * n_views % 4 == 0); the autotuner of the Python package chooses them.
+ *   classes  [n_classes] geometries (host), 1 <= n_classes <= 8, sides 64/96/128
+ *   cands    [B] descriptors (host)
+ *   ws       boac_mlem_ragged_workspace_bytes(...) bytes (device)
+ * boac_mlem_ragged = boac_mlem_ragged_prepare (sorts the candidates and
+ * copies their records into ws; not capturable in a CUDA graph: it copies
+ * from pageable host memory) + boac_mlem_ragged_run (kernel launches only:
+ * capturable, and replayable as long as ws keeps the prepared records). */
+typedef struct {
+    int cls;              /* size class: index into classes[]             */
+    int K;                /* MLEM iterations (>= 0)                       */
+    long long mu_off;     /* float offset of mu in mu_pool                */
+    long long S_off;      /* float offset of the sinogram in S_pool       */
+    long long F_off;      /* float offset of F in F_pool                  */
+} boac_ragged_cand;
+
+size_t boac_mlem_ragged_workspace_bytes(const boac_geom *classes, int n_classes,
+                                        const boac_ragged_cand *cands, int B,
+                                        const int *config);
+int boac_mlem_ragged_prepare(const boac_geom *classes, int n_classes,
+                             const boac_ragged_cand *cands, int B,
+                             const int *config, void *ws, size_t ws_bytes,
+                             void *stream);
+int boac_mlem_ragged_run(const boac_geom *classes, int n_classes,
+                         const boac_ragged_cand *cands, int B,
+                         const float *mu_pool, const float *S_pool,
+                         float *F_pool, double *L, int include_lgamma,
+                         const int *config, void *ws, size_t ws_bytes,
+                         void *stream);
+int boac_mlem_ragged(const boac_geom *classes, int n_classes,
+                     const boac_ragged_cand *cands, int B,
+                     const float *mu_pool, const float *S_pool, float *F_pool,
+                     double *L, int include_lgamma, const int *config,
+                     void *ws, size_t ws_bytes, void *stream);
+
 /* ---- boac_mlem without a workspace -------------------------------------
  * The paper has no counterpart: this is a convenience for callers that
  * cannot allocate device memory when they call the library (code running

@@ -50,6 +50,13 @@ class Tissue(ctypes.Structure):
     _fields_ = [("mu_b", ctypes.c_float), ("mu_c", ctypes.c_float), ("dR", ctypes.c_float)]
 
 
+class RaggedCand(ctypes.Structure):
+    """``boac_ragged_cand``: size class, iteration count and the float offsets
+    of the candidate's mu, sinogram and image in the three device pools."""
+    _fields_ = [("cls", ctypes.c_int), ("K", ctypes.c_int), ("mu_off", ctypes.c_longlong),
+                ("S_off", ctypes.c_longlong), ("F_off", ctypes.c_longlong)]
+
+
 class BoacError(RuntimeError):
     def __init__(self, fn: str, status: int):
         super().__init__(f"{fn} failed: {status_string(status)} ({status})")
@@ -80,6 +87,12 @@ SIGNATURES = {
     "boac_score": (_I, [_GP, _P, _P, _LL, _P, _I, _I, _P, _P, _SZ, _P]),
     "boac_loglik": (_I, [_GP, _P, _P, _LL, _I, _I, _P, _P]),
     "boac_score_grad_workspace_bytes": (_SZ, [_GP, _I, _I, _I]),
+    "boac_mlem_ragged_workspace_bytes": (_SZ, [_GP, _I, ctypes.POINTER(RaggedCand), _I, _P]),
+    "boac_mlem_ragged_prepare": (_I, [_GP, _I, ctypes.POINTER(RaggedCand), _I, _P, _P, _SZ, _P]),
+    "boac_mlem_ragged_run": (_I, [_GP, _I, ctypes.POINTER(RaggedCand), _I, _P, _P, _P, _P, _I, _P, _P,
+                                  _SZ, _P]),
+    "boac_mlem_ragged": (_I, [_GP, _I, ctypes.POINTER(RaggedCand), _I, _P, _P, _P, _P, _I, _P, _P, _SZ,
+                              _P]),
     "boac_score_grad": (_I, [_GP, _TP, _P, _P, _LL, _I, _I, _I, _I, _P, _P, _P, _P, _SZ, _P]),
 }
 

@@ -12,7 +12,7 @@ import ctypes
 import torch
 
 from . import _lib
-from ._lib import Geom, Tissue, check
+from ._lib import Geom, RaggedCand, Tissue, check
 
 
 def _ptr(t):
@@ -204,3 +204,128 @@ class BoacScore(torch.autograd.Function):
     def backward(ctx, gL):
         (grad,) = ctx.saved_tensors
         return (gL[:, None] * grad).to(ctx.c_dtype), None, None, None, None, None, None
+
+
+# ---------------------------------------------------------------- ragged
+N_CONFIGS = 6  # launch shapes per size class: 2 * shape + pair
+
+
+class RaggedBatch:
+    """Candidates of several size classes and iteration counts, packed into
+    three flat device pools (mu, sinograms, images) for boac_mlem_ragged.
+
+    ``classes``: list of Geom; ``cls``: class index per candidate; ``K``:
+    iterations per candidate; ``mu``/``S``: per-candidate tensors
+    ([n, n] and [V, n] of the candidate's class); ``F0``: initial images
+    (default ones)."""
+
+    def __init__(self, classes, cls, K, mu, S, F0=None, device=None):
+        self.classes = list(classes)
+        B = len(cls)
+        if not (len(K) == len(mu) == len(S) == B):
+            raise ValueError("cls, K, mu and S must have one entry per candidate")
+        dev = device or mu[0].device
+        geo = (Geom * len(self.classes))(*self.classes)
+        cands = (RaggedCand * B)()
+        mo = so = fo = 0
+        for b in range(B):
+            g = self.classes[int(cls[b])]
+            if tuple(mu[b].shape) != (g.n, g.n) or tuple(S[b].shape) != (g.n_views, g.n_bins):
+                raise ValueError(f"candidate {b}: tensor shapes do not match its class {g}")
+            cands[b] = RaggedCand(int(cls[b]), int(K[b]), mo, so, fo)
+            mo += g.n * g.n
+            so += g.n_views * g.n_bins
+            fo += g.n * g.n
+        self.geo, self.cands, self.B = geo, cands, B
+        self.mu_pool = torch.cat([m.reshape(-1).float() for m in mu]).to(dev).contiguous()
+        self.S_pool = torch.cat([x.reshape(-1).float() for x in S]).to(dev).contiguous()
+        if F0 is None:
+            self.F_pool = torch.ones(fo, dtype=torch.float32, device=dev)
+        else:
+            self.F_pool = torch.cat([f.reshape(-1).float() for f in F0]).to(dev).contiguous()
+        self.L = torch.empty(B, dtype=torch.float64, device=dev)
+        self.device = dev
+
+    def image(self, b: int) -> torch.Tensor:
+        g = self.classes[self.cands[b].cls]
+        o = self.cands[b].F_off
+        return self.F_pool[o:o + g.n * g.n].view(g.n, g.n)
+
+    def _config(self, config):
+        if config is None:
+            return None
+        cfg = (ctypes.c_int * len(self.classes))(*[int(c) for c in config])
+        return ctypes.cast(cfg, ctypes.c_void_p), cfg
+
+    def workspace_bytes(self, config=None) -> int:
+        c = self._config(config)
+        n = _lib.load().boac_mlem_ragged_workspace_bytes(self.geo, len(self.classes), self.cands, self.B,
+                                                         c[0] if c else None)
+        if n == 0:
+            raise ValueError("invalid ragged batch or configuration")
+        return int(n)
+
+    def prepare(self, config=None, ws=None) -> torch.Tensor:
+        """Sort the candidates and copy their records into the workspace."""
+        if ws is None:
+            ws = torch.empty(self.workspace_bytes(config), dtype=torch.uint8, device=self.device)
+        c = self._config(config)
+        check("boac_mlem_ragged_prepare", _lib.load().boac_mlem_ragged_prepare(
+            self.geo, len(self.classes), self.cands, self.B, c[0] if c else None, _ptr(ws), ws.numel(),
+            _stream(self.device)))
+        self.ws, self.config = ws, config
+        return ws
+
+    def run(self, include_lgamma: bool = True) -> torch.Tensor:
+        """Launch the per-class fused kernels (capturable in a CUDA graph)."""
+        c = self._config(self.config)
+        check("boac_mlem_ragged_run", _lib.load().boac_mlem_ragged_run(
+            self.geo, len(self.classes), self.cands, self.B, _ptr(self.mu_pool), _ptr(self.S_pool),
+            _ptr(self.F_pool), _ptr(self.L), int(include_lgamma), c[0] if c else None, _ptr(self.ws),
+            self.ws.numel(), _stream(self.device)))
+        return self.L
+
+
+def boac_mlem_ragged(batch: RaggedBatch, include_lgamma: bool = True, config=None) -> torch.Tensor:
+    """One-shot ragged MLEM + score: returns L[B] (float64); images in batch.F_pool."""
+    batch.prepare(config)
+    return batch.run(include_lgamma)
+
+
+# ---------------------------------------------------------------- graphs
+class BatchedEvaluator:
+    """The batched candidate evaluation -- rasterise mu (Eq. 3-4), K fused MLEM
+    iterations, Eq. 5 score -- captured once in a CUDA graph and replayed for
+    every new set of coefficients.  ``evaluate(c)`` copies c into the graph's
+    static input and replays; results live in ``self.L`` / ``self.F``."""
+
+    def __init__(self, g: Geom, t: Tissue, S: torch.Tensor, B: int, K: int,
+                 mode: int = _lib.RASTER_CENTER, include_lgamma: bool = True):
+        dev = S.device
+        self.g, self.t, self.K, self.mode, self.lg = g, t, int(K), mode, include_lgamma
+        self.c = torch.zeros(B, 6, dtype=torch.float32, device=dev)
+        self.S = S.contiguous()
+        self.mu = torch.empty(B, g.n, g.n, dtype=torch.float32, device=dev)
+        self.F = torch.empty(B, g.n, g.n, dtype=torch.float32, device=dev)
+        self.L = torch.empty(B, dtype=torch.float64, device=dev)
+        self.ws = workspace(g, B, _lib.OP_MLEM, dev)
+        self.c.copy_(torch.tensor([[8.0, 0, 0, 0, 0, 0]], device=dev).expand(B, 6))
+        side = torch.cuda.Stream(dev)
+        side.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(side):  # warm-up outside capture (sets kernel attributes)
+            self._body()
+        torch.cuda.current_stream(dev).wait_stream(side)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self._body()
+
+    def _body(self):
+        boac_rasterize_mu(self.g, self.t, self.c, self.mode, out=self.mu)
+        self.F.fill_(1.0)
+        boac_mlem(self.g, self.mu, self.S, self.F, self.K, score=True, include_lgamma=self.lg,
+                  ws=self.ws, L=self.L)
+
+    def evaluate(self, c: torch.Tensor) -> torch.Tensor:
+        self.c.copy_(c, non_blocking=True)
+        self.graph.replay()
+        return self.L

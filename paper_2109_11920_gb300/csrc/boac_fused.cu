@@ -29,10 +29,19 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "boac_device.cuh"
 #include "boac_internal.h"
 
 namespace boac {
+
+struct RaggedDesc {
+    long long mu_off, S_off, F_off;  // float offsets into the caller's pools
+    int K;                           // MLEM iterations of this candidate
+    int out;                         // index of its score in L
+};
 
 struct FusedArgs {
     const float* mu;
@@ -47,6 +56,15 @@ struct FusedArgs {
     // read with plain (coherent) loads, never through the read-only path.
     float* tab;   // [slots][tab_floats]: attenuation exponents, see below
     float* sens;  // [slots][n][n]
+    // Images above 128 x 128 do not fit shared memory: their F, accumulator
+    // and sample buffer live in a per-slot region of the workspace instead
+    // (same layout), read through L1 and written through to L2.
+    float* img;   // [slots][2 IMG + n WP] or unused
+    // Ragged batches: per-candidate records (device) and a work counter that
+    // CTAs advance with atomicAdd (largest K first, set up by the host).
+    // nullptr: uniform batch, candidate b at b * n^2 / b * s_stride, K = K.
+    const RaggedDesc* desc;
+    int* counter;
 };
 
 // Shared-memory and work layout of one CTA (image side N, NT threads).
@@ -83,10 +101,20 @@ __host__ __device__ constexpr size_t fused_tab_floats(int n, int V) {
     return (size_t)(V / 2) * ((size_t)n * n + (size_t)n);
 }
 
+// Whether the images of an n x n candidate live in global memory.
+__host__ __device__ constexpr bool fused_global_images(int n) { return n > 128; }
+
+template <int N, int NT>
+__host__ __device__ constexpr size_t fused_image_floats() {
+    using L = FusedShape<N, NT>;
+    return 2 * (size_t)L::IMG + (size_t)N * L::WP;
+}
+
 template <int N, int NT>
 __host__ __device__ constexpr size_t fused_smem_bytes(int V) {
     using L = FusedShape<N, NT>;
-    return sizeof(float) * (2 * L::IMG + N * L::WP + 4 * L::NSEG * N + 4 * N + 2 * ((V + 1) / 2) * 2) +
+    return sizeof(float) * ((fused_global_images(N) ? 0 : fused_image_floats<N, NT>()) +
+                            4 * L::NSEG * N + 4 * N + 2 * ((V + 1) / 2) * 2) +
            sizeof(double) * 32;
 }
 
@@ -126,13 +154,16 @@ __device__ __forceinline__ double loglik_term(double s, double q, int include_lg
     return t;
 }
 
-// CTAs per SM the register allocation is sized for (shared memory allows
-// three 64x64 CTAs per SM, one of the larger sizes).
-template <int N>
-constexpr int fused_min_blocks() { return N <= 64 ? 3 : 1; }
+// CTAs per SM the register allocation is sized for: as many as shared memory
+// allows (three 64x64 CTAs, one of the larger sizes), but no fewer than 64
+// registers per thread.
+template <int N, int NT>
+constexpr int fused_min_blocks() {
+    return (N <= 64 ? 3 : 1) < 1024 / NT ? (N <= 64 ? 3 : 1) : (1024 / NT > 0 ? 1024 / NT : 1);
+}
 
 template <int N, int NT, bool QUAD>
-__global__ void __launch_bounds__(NT, fused_min_blocks<N>()) mlem_fused_kernel(FusedArgs a) {
+__global__ void __launch_bounds__(NT, (fused_min_blocks<N, NT>())) mlem_fused_kernel(FusedArgs a) {
     using Lay = FusedShape<N, NT>;
     constexpr int P = Lay::P, IMG = Lay::IMG, NN = Lay::NN, WP = Lay::WP;
     constexpr int NSEG = Lay::NSEG, SEG = Lay::SEG;
@@ -140,10 +171,13 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<N>()) mlem_fused_kernel(F
     static_assert(!QUAD || NT >= 2 * N, "row views need 2N threads in the ratio step");
 
     extern __shared__ __align__(16) float smem[];
-    float* img0 = smem;                 // F (mu during set-up), padded
+    float* const img_base = fused_global_images(N)
+                                ? a.img + (size_t)blockIdx.x * fused_image_floats<N, NT>()
+                                : smem;
+    float* img0 = img_base;             // F (mu during set-up), padded
     float* img1 = img0 + IMG;           // back-projection accumulator, padded
     float* W = img1 + IMG;              // [N][WP] grid samples / weights
-    float* redc = W + N * WP;           // [2][NSEG][N] column partial sums
+    float* redc = fused_global_images(N) ? smem : W + N * WP;  // [2][NSEG][N] column partial sums
     float* redr = redc + 2 * NSEG * N;  // [2][NSEG][N] row partial sums
     float* rr = redr + 2 * NSEG * N;    // [4][N] ratios r = S / q per view
     float* csn = rr + 4 * N;            // [V][2]
@@ -166,9 +200,20 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<N>()) mlem_fused_kernel(F
     float* tab = a.tab + (size_t)blockIdx.x * fused_tab_floats(N, V);
     float* sens = a.sens + (size_t)blockIdx.x * NN;
 
-    for (int cand = blockIdx.x; cand < a.B; cand += gridDim.x) {
-        const float* __restrict__ S = a.S + (size_t)cand * a.s_stride;
-        const float* __restrict__ mu = a.mu + (size_t)cand * NN;
+    __shared__ int next_cand;
+    for (int cand = blockIdx.x;; cand += gridDim.x) {
+        if (a.desc) {  // ragged: take the next candidate from the queue
+            if (tid == 0) next_cand = atomicAdd(a.counter, 1);
+            __syncthreads();
+            cand = next_cand;
+        }
+        if (cand >= a.B) break;
+        const RaggedDesc* d = a.desc ? a.desc + cand : nullptr;
+        const float* __restrict__ S = a.S + (d ? d->S_off : (long long)cand * a.s_stride);
+        const float* __restrict__ mu = a.mu + (d ? d->mu_off : (long long)cand * NN);
+        float* Fc = a.F + (d ? d->F_off : (long long)cand * NN);
+        const int Kc = d ? d->K : a.K;
+        const int lidx = d ? d->out : cand;
 
         // ---- set-up: mu -> img0 (zero ring), img1 = 0
         for (int i = tid; i < IMG; i += NT) {
@@ -258,7 +303,7 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<N>()) mlem_fused_kernel(F
         for (int i = tid; i < NN; i += NT) {
             const int pi = (i / N + 1) * P + (i % N) + 1;
             sens[i] = img1[pi];
-            img0[pi] = a.F[(size_t)cand * NN + i];
+            img0[pi] = Fc[i];
         }
         __syncthreads();
         for (int i = tid; i < IMG; i += NT) img1[i] = 0.0f;
@@ -266,8 +311,8 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<N>()) mlem_fused_kernel(F
 
         // ---- MLEM iterations, then one more forward pass for the score
         double lacc = 0.0;
-        for (int it = 0; it <= a.K; ++it) {
-            const bool scoring = (it == a.K);
+        for (int it = 0; it <= Kc; ++it) {
+            const bool scoring = (it == Kc);
             if (scoring && !a.L) break;
             for (int gi = 0; gi < ngrid; ++gi) {
                 const float cs = csn[2 * gi], sn = csn[2 * gi + 1];
@@ -378,107 +423,156 @@ __global__ void __launch_bounds__(NT, fused_min_blocks<N>()) mlem_fused_kernel(F
             if (tid == 0) {
                 double t = 0.0;
                 for (int wi = 0; wi < NT / 32; ++wi) t += dred[wi];
-                a.L[cand] = t;
+                a.L[lidx] = t;
             }
         }
 
         // ---- F^K out
-        for (int i = tid; i < NN; i += NT) a.F[(size_t)cand * NN + i] = img0[(i / N + 1) * P + (i % N) + 1];
+        for (int i = tid; i < NN; i += NT) Fc[i] = img0[(i / N + 1) * P + (i % N) + 1];
         __syncthreads();
     }
 }
 
 // ---------------------------------------------------------------- host side
+// Launch shapes: for each image side, CTAs of 2n, 4n or 8n threads (at most
+// 1024), with four or two views per sample grid.  Configuration id =
+// 2 * shape + (1 for two views per grid).
+constexpr int kShapes = 3;
+constexpr int kConfigs = 2 * kShapes;
+
+struct FusedVariant {
+    int n, nt;
+    bool quad;
+    size_t (*smem)(int V);
+    const void* func;
+    int (*launch)(const FusedArgs& a, int slots, cudaStream_t st);
+};
+
 template <int N, int NT, bool QUAD>
-static int fused_occupancy(int V) {
-    constexpr int kDev = 16;
-    static int cached[kDev][kMaxViews + 1];  // 0 = not yet computed
+static int fused_launch_t(const FusedArgs& a, int slots, cudaStream_t st) {
+    // once per device: allow the large dynamic shared-memory carve-out
+    constexpr int kDev = 64;
+    static bool attr_set[kDev];
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) { cudaGetLastError(); return 0; }
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kDev) return launch_status();
+    if (!attr_set[dev]) {
+        if (cudaFuncSetAttribute(mlem_fused_kernel<N, NT, QUAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)fused_smem_bytes<N, NT>(kMaxViews)) != cudaSuccess)
+            return launch_status();
+        attr_set[dev] = true;
+    }
+    mlem_fused_kernel<N, NT, QUAD><<<slots, NT, fused_smem_bytes<N, NT>(a.V), st>>>(a);
+    return launch_status();
+}
+
+template <int N, int NT>
+static size_t smem_of(int V) { return fused_smem_bytes<N, NT>(V); }
+
+template <int N, int NT, bool QUAD>
+static FusedVariant make_variant() {
+    return FusedVariant{N, NT, QUAD, smem_of<N, NT>, (const void*)mlem_fused_kernel<N, NT, QUAD>,
+                        fused_launch_t<N, NT, QUAD>};
+}
+
+#define BOAC_SHAPES(NV)                                                                        \
+    {make_variant<NV, 2 * NV, true>(), make_variant<NV, 2 * NV, false>(),                      \
+     make_variant<NV, 4 * NV, true>(), make_variant<NV, 4 * NV, false>(),                      \
+     make_variant<NV, (8 * NV > 1024 ? 1024 : 8 * NV), true>(),                                \
+     make_variant<NV, (8 * NV > 1024 ? 1024 : 8 * NV), false>()}
+
+static const FusedVariant* variant_table(int n) {
+    static const FusedVariant t64[kConfigs] = BOAC_SHAPES(64);
+    static const FusedVariant t96[kConfigs] = BOAC_SHAPES(96);
+    static const FusedVariant t128[kConfigs] = BOAC_SHAPES(128);
+    static const FusedVariant t256[kConfigs] = BOAC_SHAPES(256);
+    switch (n) {
+        case 64: return t64;
+        case 96: return t96;
+        case 128: return t128;
+        case 256: return t256;
+        default: return nullptr;
+    }
+}
+
+// Default configuration: the largest CTA that keeps >= 64 registers per
+// thread at the occupancy shared memory allows; four views per grid when
+// V % 4 == 0.
+static int default_config(const boac_geom* g) {
+    const int shape = g->n == 64 ? 1 : 2;
+    return 2 * shape + (g->n_views % 4 == 0 ? 0 : 1);
+}
+
+static const FusedVariant* get_variant(const boac_geom* g, int config) {
+    const FusedVariant* t = variant_table(g->n);
+    if (!t || config < 0 || config >= kConfigs) return nullptr;
+    const FusedVariant* v = &t[config];
+    if (v->quad ? (g->n_views % 4 != 0) : (g->n_views % 2 != 0)) return nullptr;
+    return v;
+}
+
+static int variant_occupancy(const FusedVariant* v, int V) {
+    constexpr int kDev = 64;
+    static int cached[kDev][4][kConfigs][kMaxViews + 1];  // 0 = not yet computed
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) {
+        cudaGetLastError();
+        return 0;
+    }
+    const int ni = v->n == 64 ? 0 : (v->n == 96 ? 1 : (v->n == 128 ? 2 : 3));
+    const int ci = (int)(v - variant_table(v->n));
     if (V < 0 || V > kMaxViews) return 0;
-    if (dev < kDev && cached[dev][V]) return cached[dev][V];
-    size_t smem = fused_smem_bytes<N, NT>(V);
-    if (cudaFuncSetAttribute(mlem_fused_kernel<N, NT, QUAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess) {
+    if (dev < kDev && cached[dev][ni][ci][V]) return cached[dev][ni][ci][V];
+    if (cudaFuncSetAttribute(v->func, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)v->smem(kMaxViews)) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, mlem_fused_kernel<N, NT, QUAD>, NT, smem) !=
-        cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, v->func, v->nt, v->smem(V)) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
-    if (dev < kDev) cached[dev][V] = nb;
+    if (dev < kDev) cached[dev][ni][ci][V] = nb;
     return nb;
 }
-
-template <int N, int NT, bool QUAD>
-static int fused_launch_t(const FusedArgs& a, int slots, cudaStream_t st) {
-    size_t smem = fused_smem_bytes<N, NT>(a.V);
-    if (cudaFuncSetAttribute(mlem_fused_kernel<N, NT, QUAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
-        return launch_status();
-    mlem_fused_kernel<N, NT, QUAD><<<slots, NT, smem, st>>>(a);
-    return launch_status();
-}
-
-// Four views per sample grid when the view count allows it, else two.
-template <int N, int NT>
-static int fused_launch(const FusedArgs& a, int slots, cudaStream_t st) {
-    return (a.V % 4 == 0) ? fused_launch_t<N, NT, true>(a, slots, st)
-                          : fused_launch_t<N, NT, false>(a, slots, st);
-}
-
-// Dispatch on the image side: (N, threads per CTA).
-#define BOAC_FUSED_SIZES(X) X(64, 256) X(96, 768) X(128, 1024)
 
 // Workspace for `slots` CTA slots: the attenuation-exponent tables, then the
 // sensitivity images.  Returns the total bytes; *sens_off the offset of the
 // sensitivity images.
-static size_t fused_slot_layout(const boac_geom* g, int slots, size_t* sens_off = nullptr) {
+static size_t fused_slot_layout(const boac_geom* g, int slots, size_t* sens_off = nullptr,
+                                size_t* img_off = nullptr) {
     const size_t tab = align256(sizeof(float) * (size_t)slots * fused_tab_floats(g->n, g->n_views));
+    const size_t sens = align256(sizeof(float) * (size_t)slots * g->n * g->n);
     if (sens_off) *sens_off = tab;
-    return tab + align256(sizeof(float) * (size_t)slots * g->n * g->n);
+    if (img_off) *img_off = tab + sens;
+    // padded F and accumulator, (n+1)(n+2)+1 floats each, and the n x (n+1)
+    // sample buffer, for sides held in global memory
+    const size_t img_floats = fused_global_images(g->n)
+                                  ? 2 * ((size_t)(g->n + 1) * (g->n + 2) + 1) + (size_t)g->n * (g->n + 1)
+                                  : 0;
+    return tab + sens + align256(sizeof(float) * (size_t)slots * img_floats);
 }
 
-int fused_slots(const boac_geom* g, int B) {
-    int per_sm = 0;
-#define X(NV, TV)                                                                   \
-    if (g->n == NV)                                                                 \
-        per_sm = (g->n_views % 4 == 0) ? fused_occupancy<NV, TV, true>(g->n_views) \
-                                       : fused_occupancy<NV, TV, false>(g->n_views);
-    BOAC_FUSED_SIZES(X)
-#undef X
+static int variant_slots(const boac_geom* g, const FusedVariant* v, int B) {
+    const int per_sm = variant_occupancy(v, g->n_views);
     if (per_sm <= 0) return 0;
-    long long slots = (long long)per_sm * sm_count();
+    const long long slots = (long long)per_sm * sm_count();
     return (int)(slots < B ? slots : B);
 }
 
-size_t fused_workspace_bytes(const boac_geom* g, int B) {
-    int slots = fused_slots(g, B);
-    if (slots <= 0) return 0;
-    return fused_slot_layout(g, slots);
+int fused_slots(const boac_geom* g, int B) {
+    const FusedVariant* v = get_variant(g, default_config(g));
+    return v ? variant_slots(g, v, B) : 0;
 }
 
-}  // namespace boac
+size_t fused_workspace_bytes(const boac_geom* g, int B) {
+    const int slots = fused_slots(g, B);
+    return slots > 0 ? fused_slot_layout(g, slots) : 0;
+}
 
-using namespace boac;
-
-extern "C" int boac_mlem(const boac_geom* g, const float* mu, const float* S, long long s_stride,
-                         float* F, int K, int B, double* L, int include_lgamma, void* ws,
-                         size_t ws_bytes, void* stream) {
-    if (!geom_ok(g) || !mu || !S || !F || B < 1 || K < 0 || s_stride < 0) return BOAC_EINVAL;
-    if (g->n_views % 2) return BOAC_EINVAL;
-    bool have = false;
-#define X(NV, TV) have |= (g->n == NV);
-    BOAC_FUSED_SIZES(X)
-#undef X
-    if (!have) return BOAC_EUNSUPPORTED;
-    int slots = fused_slots(g, B);
-    if (slots <= 0) return BOAC_ECUDA;
-    size_t need = fused_workspace_bytes(g, B);
-    if (!ws || ws_bytes < need) return BOAC_EWORKSPACE;
+static FusedArgs uniform_args(const boac_geom* g, const float* mu, const float* S, long long s_stride,
+                              float* F, int K, int B, double* L, int include_lgamma, void* scratch,
+                              int slots) {
     FusedArgs a;
     a.mu = mu;
     a.S = S;
@@ -490,16 +584,150 @@ extern "C" int boac_mlem(const boac_geom* g, const float* mu, const float* S, lo
     a.V = g->n_views;
     a.K = K;
     a.dx = g->pixel_cm;
-    size_t sens_off = 0;
-    fused_slot_layout(g, slots, &sens_off);
-    a.tab = static_cast<float*>(ws);
-    a.sens = reinterpret_cast<float*>(static_cast<char*>(ws) + sens_off);
+    size_t sens_off = 0, img_off = 0;
+    fused_slot_layout(g, slots, &sens_off, &img_off);
+    a.tab = static_cast<float*>(scratch);
+    a.sens = reinterpret_cast<float*>(static_cast<char*>(scratch) + sens_off);
+    a.img = reinterpret_cast<float*>(static_cast<char*>(scratch) + img_off);
+    a.desc = nullptr;
+    a.counter = nullptr;
+    return a;
+}
+
+// ---------------------------------------------------------------- ragged
+struct RaggedPlan {
+    int cls_count[kMaxRaggedClasses];
+    int slots[kMaxRaggedClasses];
+    const FusedVariant* var[kMaxRaggedClasses];
+    size_t desc_off[kMaxRaggedClasses], tab_off[kMaxRaggedClasses], counter_off, total;
+};
+
+static int ragged_plan(const boac_geom* classes, int n_classes, const boac_ragged_cand* cands, int B,
+                       const int* config, RaggedPlan* pl) {
+    if (!classes || n_classes < 1 || n_classes > kMaxRaggedClasses || !cands || B < 1) return BOAC_EINVAL;
+    for (int c = 0; c < n_classes; ++c) {
+        if (!geom_ok(&classes[c]) || classes[c].n_views % 2) return BOAC_EINVAL;
+        pl->cls_count[c] = 0;
+    }
+    for (int b = 0; b < B; ++b) {
+        const boac_ragged_cand& d = cands[b];
+        if (d.cls < 0 || d.cls >= n_classes || d.K < 0 || d.mu_off < 0 || d.S_off < 0 || d.F_off < 0)
+            return BOAC_EINVAL;
+        pl->cls_count[d.cls]++;
+    }
+    size_t off = 0;
+    for (int c = 0; c < n_classes; ++c) {
+        if (!variant_table(classes[c].n)) return BOAC_EUNSUPPORTED;
+        const int cfg = config ? config[c] : default_config(&classes[c]);
+        pl->var[c] = get_variant(&classes[c], cfg);
+        if (!pl->var[c]) return BOAC_EINVAL;
+        pl->slots[c] = pl->cls_count[c] ? variant_slots(&classes[c], pl->var[c], pl->cls_count[c]) : 0;
+        if (pl->cls_count[c] && pl->slots[c] <= 0) return BOAC_ECUDA;
+        pl->desc_off[c] = off;
+        off += align256(sizeof(RaggedDesc) * (size_t)pl->cls_count[c]);
+        pl->tab_off[c] = off;
+        off += pl->slots[c] ? fused_slot_layout(&classes[c], pl->slots[c]) : 0;
+    }
+    pl->counter_off = off;
+    off += align256(sizeof(int) * kMaxRaggedClasses);
+    pl->total = off;
+    return BOAC_OK;
+}
+
+}  // namespace boac
+
+using namespace boac;
+
+extern "C" int boac_mlem(const boac_geom* g, const float* mu, const float* S, long long s_stride,
+                         float* F, int K, int B, double* L, int include_lgamma, void* ws,
+                         size_t ws_bytes, void* stream) {
+    if (!geom_ok(g) || !mu || !S || !F || B < 1 || K < 0 || s_stride < 0) return BOAC_EINVAL;
+    if (g->n_views % 2) return BOAC_EINVAL;
+    const FusedVariant* v = get_variant(g, default_config(g));
+    if (!v) return BOAC_EUNSUPPORTED;
+    const int slots = variant_slots(g, v, B);
+    if (slots <= 0) return BOAC_ECUDA;
+    if (!ws || ws_bytes < fused_slot_layout(g, slots)) return BOAC_EWORKSPACE;
+    const FusedArgs a = uniform_args(g, mu, S, s_stride, F, K, B, L, include_lgamma, ws, slots);
+    return v->launch(a, slots, as_stream(stream));
+}
+
+extern "C" size_t boac_mlem_ragged_workspace_bytes(const boac_geom* classes, int n_classes,
+                                                   const boac_ragged_cand* cands, int B,
+                                                   const int* config) {
+    RaggedPlan pl;
+    return ragged_plan(classes, n_classes, cands, B, config, &pl) == BOAC_OK ? pl.total : 0;
+}
+
+extern "C" int boac_mlem_ragged_prepare(const boac_geom* classes, int n_classes,
+                                        const boac_ragged_cand* cands, int B, const int* config,
+                                        void* ws, size_t ws_bytes, void* stream) {
+    RaggedPlan pl;
+    int s = ragged_plan(classes, n_classes, cands, B, config, &pl);
+    if (s != BOAC_OK) return s;
+    if (!ws || ws_bytes < pl.total) return BOAC_EWORKSPACE;
+    // Per-class records, largest K first (longest-processing-time order for
+    // the CTAs' shared work queue).  Copied from pageable host memory, so
+    // the copy is staged before this call returns.
+    std::vector<RaggedDesc> host((size_t)B);
+    std::vector<int> order((size_t)B);
+    for (int b = 0; b < B; ++b) order[b] = b;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        if (cands[x].cls != cands[y].cls) return cands[x].cls < cands[y].cls;
+        return cands[x].K > cands[y].K;
+    });
+    for (int i = 0; i < B; ++i) {
+        const boac_ragged_cand& d = cands[order[i]];
+        host[i] = RaggedDesc{d.mu_off, d.S_off, d.F_off, d.K, order[i]};
+    }
+    char* base = static_cast<char*>(ws);
+    int first = 0;
+    for (int c = 0; c < n_classes; ++c) {
+        const int cnt = pl.cls_count[c];
+        if (cnt == 0) continue;
+        if (cudaMemcpyAsync(base + pl.desc_off[c], host.data() + first, sizeof(RaggedDesc) * cnt,
+                            cudaMemcpyHostToDevice, as_stream(stream)) != cudaSuccess)
+            return launch_status();
+        first += cnt;
+    }
+    return BOAC_OK;
+}
+
+extern "C" int boac_mlem_ragged_run(const boac_geom* classes, int n_classes,
+                                    const boac_ragged_cand* cands, int B, const float* mu_pool,
+                                    const float* S_pool, float* F_pool, double* L, int include_lgamma,
+                                    const int* config, void* ws, size_t ws_bytes, void* stream) {
+    if (!mu_pool || !S_pool || !F_pool || !L) return BOAC_EINVAL;
+    RaggedPlan pl;
+    int s = ragged_plan(classes, n_classes, cands, B, config, &pl);
+    if (s != BOAC_OK) return s;
+    if (!ws || ws_bytes < pl.total) return BOAC_EWORKSPACE;
+    char* base = static_cast<char*>(ws);
     cudaStream_t st = as_stream(stream);
-#define X(NV, TV) \
-    if (g->n == NV) return fused_launch<NV, TV>(a, slots, st);
-    BOAC_FUSED_SIZES(X)
-#undef X
-    return BOAC_EUNSUPPORTED;
+    if (cudaMemsetAsync(base + pl.counter_off, 0, sizeof(int) * kMaxRaggedClasses, st) != cudaSuccess)
+        return launch_status();
+    for (int c = 0; c < n_classes; ++c) {
+        const int cnt = pl.cls_count[c];
+        if (cnt == 0) continue;
+        FusedArgs a = uniform_args(&classes[c], mu_pool, S_pool, 0, F_pool, 0, cnt, L, include_lgamma,
+                                   base + pl.tab_off[c], pl.slots[c]);
+        a.desc = reinterpret_cast<const RaggedDesc*>(base + pl.desc_off[c]);
+        a.counter = reinterpret_cast<int*>(base + pl.counter_off) + c;
+        s = pl.var[c]->launch(a, pl.slots[c], st);
+        if (s != BOAC_OK) return s;
+    }
+    return BOAC_OK;
+}
+
+extern "C" int boac_mlem_ragged(const boac_geom* classes, int n_classes, const boac_ragged_cand* cands,
+                                int B, const float* mu_pool, const float* S_pool, float* F_pool,
+                                double* L, int include_lgamma, const int* config, void* ws,
+                                size_t ws_bytes, void* stream) {
+    if (!mu_pool || !S_pool || !F_pool || !L) return BOAC_EINVAL;
+    int s = boac_mlem_ragged_prepare(classes, n_classes, cands, B, config, ws, ws_bytes, stream);
+    if (s != BOAC_OK) return s;
+    return boac_mlem_ragged_run(classes, n_classes, cands, B, mu_pool, S_pool, F_pool, L,
+                                include_lgamma, config, ws, ws_bytes, stream);
 }
 
 // ---------------------------------------------------------------------------
@@ -557,37 +785,15 @@ extern "C" int boac_mlem_noalloc(const boac_geom* g, const float* mu, const floa
                                  int include_lgamma, void* stream) {
     if (!geom_ok(g) || !mu || !S || !F || B < 1 || K < 0 || s_stride < 0) return BOAC_EINVAL;
     if (g->n_views % 2) return BOAC_EINVAL;
-    bool have = false;
-#define X(NV, TV) have |= (g->n == NV);
-    BOAC_FUSED_SIZES(X)
-#undef X
-    if (!have) return BOAC_EUNSUPPORTED;
+    const FusedVariant* v = get_variant(g, default_config(g));
+    if (!v) return BOAC_EUNSUPPORTED;
     if (fused_slots(g, B) <= 0) return BOAC_ECUDA;
     const int slots = noalloc_slots(g, B);
     if (slots <= 0) return BOAC_EWORKSPACE;  // one candidate's scratch exceeds 64 MiB
     void* scratch = noalloc_scratch_ptr();
     if (!scratch) return BOAC_ECUDA;
-    FusedArgs a;
-    a.mu = mu;
-    a.S = S;
-    a.s_stride = s_stride;
-    a.F = F;
-    a.L = L;
-    a.include_lgamma = include_lgamma;
-    a.B = B;
-    a.V = g->n_views;
-    a.K = K;
-    a.dx = g->pixel_cm;
     // The kernel writes every table entry and sensitivity pixel of a slot
     // before reading it, so the scratch needs no clearing between calls.
-    size_t sens_off = 0;
-    fused_slot_layout(g, slots, &sens_off);
-    a.tab = static_cast<float*>(scratch);
-    a.sens = reinterpret_cast<float*>(static_cast<char*>(scratch) + sens_off);
-    cudaStream_t st = as_stream(stream);
-#define X(NV, TV) \
-    if (g->n == NV) return fused_launch<NV, TV>(a, slots, st);
-    BOAC_FUSED_SIZES(X)
-#undef X
-    return BOAC_EUNSUPPORTED;
+    const FusedArgs a = uniform_args(g, mu, S, s_stride, F, K, B, L, include_lgamma, scratch, slots);
+    return v->launch(a, slots, as_stream(stream));
 }

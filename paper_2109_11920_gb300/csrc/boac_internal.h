@@ -12,6 +12,8 @@ namespace boac {
 // Largest supported image side and view count.
 constexpr int kMaxN = 256;
 constexpr int kMaxViews = 720;
+// Largest number of size classes in one ragged batch.
+constexpr int kMaxRaggedClasses = 8;
 
 // Geometry checks shared by every entry point: n in [8, kMaxN], n_bins == n,
 // bin_cm == pixel_cm > 0, n_views in [1, kMaxViews].

@@ -111,3 +111,12 @@ def ragged_schedule(rng: np.random.Generator, B: int = 512, mix=(1, 1, 2), k_ran
     rng.shuffle(cls)
     K = rng.integers(k_range[0], k_range[1] + 1, size=B).astype(np.int32)
     return cls, K
+
+
+def slice_coefficients(rng: np.random.Generator, n_slices: int, base=C_TRUE) -> np.ndarray:
+    """Per-slice true head coefficients for the large-slice workload:
+    c_0 ~ U(6, 9) cm, c_1..c_5 = base_k x U(0.5, 1.5)."""
+    c = np.empty((n_slices, 6))
+    c[:, 0] = rng.uniform(6.0, 9.0, n_slices)
+    c[:, 1:] = np.asarray(base[1:])[None, :] * rng.uniform(0.5, 1.5, (n_slices, 5))
+    return c

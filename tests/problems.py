@@ -35,17 +35,17 @@ class Problem:
 
 
 def make_problem(n: int, dx: float, V: int, counts: float, B: int, seed: int = 0,
-                 mode: int = oracle.CENTER) -> Problem:
+                 mode: int = oracle.CENTER, c_true=synth.C_TRUE) -> Problem:
     dx = f32(dx)
     tissue = tuple(f32(t) for t in synth.TISSUE)
     mu_b, mu_c, dR = tissue
     ph, noise, cand = synth.streams(seed)
-    c_true = np.array(synth.C_TRUE, dtype=F32).astype(np.float64)
+    c_true = np.array(c_true, dtype=F32).astype(np.float64)
     g = oracle.Geometry(n, dx, V)
     mu_true = oracle.rasterize(n, dx, mu_b, mu_c, dR, c_true, oracle.CENTER)
     F_true = synth.paint_activity(n, dx, mu_true == mu_b, synth.ellipses(ph, c_true[0]))
     S = synth.poisson_sinogram(noise, oracle.project(g, mu_true, F_true), counts)
-    coefs = synth.candidates(cand, B).astype(F32).astype(np.float64)
+    coefs = synth.candidates(cand, B, c_true).astype(F32).astype(np.float64)
     mu = np.stack([oracle.rasterize(n, dx, mu_b, mu_c, dR, c, mode) for c in coefs])
     return Problem(n, dx, V, tissue, mu_true, F_true, S, coefs, mu)
 
