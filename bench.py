@@ -165,6 +165,17 @@ def profiled_traffic():
     return float(m_b.group(1))
 
 
+# FP32 work per ray sample per view per iteration: two bilinear gathers (F and
+# mu), the attenuation scan and exponential, the accumulation, and the
+# transposed bilinear scatter of the back-projection.
+FLOPS_PER_SAMPLE = 50
+
+
+def fp32_peak_tflops():
+    """FP32 FMA rate: 152 SMs x 128 lanes x 2 flop x 2070 MHz (max SM clock)."""
+    return 152 * 128 * 2 * 2.070e9 / 1e12
+
+
 def algorithmic_bytes_per_cand_iter(n, V):
     """Per candidate-iteration: the attenuation table read in the forward and
     in the backward pass (2 x 4 V n^2 bytes), plus F read+write, sens read
@@ -296,15 +307,27 @@ def run_gpu(args, rank, world, local_rank):
 
     # ---- roofline of the dominant kernel (the fused MLEM kernel)
     kavg_s = sum(kern_ms) / len(kern_ms) / 1e3
-    alg = algorithmic_bytes_per_cand_iter(WL.n, WL.V) * B * K
-    peak, peak_kind = measured_peak_gbs()
-    achieved = alg / kavg_s / 1e9
+    cand_its = B * K
     traffic = profiled_traffic() if (B, K) == (WL.B, WL.K) else None
-    roof = {"bound": "hbm", "kernel": "mlem_fused_kernel<128,1024>", "achieved": achieved,
-            "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-            "peak_kind": f"{peak_kind} hbm_gbs (copy)",
-            "algorithmic_bytes_per_launch": alg,
-            "kernel_ms": 1e3 * kavg_s}
+    # On-chip bound (ALU/issue): the algorithm's FP32 work per candidate-
+    # iteration against the FP32 FMA rate of the part.
+    flops = FLOPS_PER_SAMPLE * WL.V * WL.n * WL.n * cand_its
+    fp32_peak = fp32_peak_tflops()
+    achieved = flops / kavg_s / 1e12
+    roof = {"bound": "alu", "kernel": "mlem_fused_kernel<128,1024,4 views per grid>",
+            "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+            "traffic": traffic,
+            "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+            "work_model": f"{FLOPS_PER_SAMPLE} FP32 ops per ray sample per view per iteration",
+            "algorithmic_flops_per_launch": flops, "kernel_ms": 1e3 * kavg_s}
+    # The same launch against HBM: bytes of the materialised-table algorithm
+    # (attenuation table read in the forward and the backward pass).
+    peak, peak_kind = measured_peak_gbs()
+    alg = algorithmic_bytes_per_cand_iter(WL.n, WL.V) * cand_its
+    hbm = {"achieved": alg / kavg_s / 1e9, "peak": peak, "unit": "GB/s",
+           "frac": alg / kavg_s / 1e9 / peak, "peak_kind": f"{peak_kind} hbm_gbs (copy)",
+           "algorithmic_bytes_per_launch": alg,
+           "dram_bytes_per_launch": traffic}
     config = dict(CONFIG, global_batch=world * B, parallelism=f"replicas{world}")
     if (B, K) != (WL.B, WL.K):
         config["reduced_case"] = f"{B} candidates x {K} iterations (not the benchmark workload)"
@@ -314,6 +337,7 @@ def run_gpu(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": config,
         "roofline": roof,
+        "roofline_hbm": hbm,
         "e2e": e2e,
         "gpu_launches": 2 * args.steps,
         "clocks": clk.summary(),
