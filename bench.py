@@ -183,6 +183,24 @@ def algorithmic_bytes_per_cand_iter(n, V):
     return 8.0 * V * n * n + 4.0 * (3 * n * n + V * n)
 
 
+# ----------------------------------------------------------------- ranks
+def max_over_ranks(x: float, world: int) -> float:
+    """Largest value of x over all ranks (the job's wall time); identity at N=1."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_value(world: int, per_rank_units: int, steps: int, max_ms: float) -> float:
+    """Whole-job throughput: every rank's units over the slowest rank's time."""
+    return world * per_rank_units * steps / (max_ms / 1e3)
+
+
 # ----------------------------------------------------------------- reference arm
 def run_reference(args, rank, world):
     import oracle
@@ -289,12 +307,8 @@ def run_gpu(args, rank, world, local_rank):
     barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     kern_ms = [a.elapsed_time(b) for a, b in evk]
-    tot_ms = sum(step_ms)
-    if world > 1:
-        tt = torch.tensor([tot_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        tot_ms = float(tt.item())
-    value = world * B * K * args.steps / (tot_ms / 1e3)
+    tot_ms = max_over_ranks(sum(step_ms), world)
+    value = weak_scaling_value(world, B * K, args.steps, tot_ms)
     assert torch.isfinite(L).all(), "non-finite score"
 
     # ---- end to end through the public API with host buffers (pinned)
@@ -379,12 +393,8 @@ def e2e_timing(args, world, dev, stream, step, c_d, S_d, L, F, coefs, S_np, flus
         b.record(stream)
         b.synchronize()
         e_ms.append(a.elapsed_time(b))
-    e_tot = sum(e_ms)
-    if world > 1:
-        tt = torch.tensor([e_tot], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e_tot = float(tt.item())
-    return {"value": world * B * K * args.steps / (e_tot / 1e3), "unit": UNIT,
+    e_tot = max_over_ranks(sum(e_ms), world)
+    return {"value": weak_scaling_value(world, B * K, args.steps, e_tot), "unit": UNIT,
             "h2d_bytes_per_step": c_h.numel() * 4 + S_h.numel() * 4,
             "d2h_bytes_per_step": L_h.numel() * 8 + F_h.numel() * 4}
 
