@@ -146,6 +146,11 @@ __device__ __forceinline__ float ex2(float x) {
     return y;
 }
 
+// Ask L2 to fetch the 128-byte line holding p (no register result).
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 __device__ __forceinline__ double loglik_term(double s, double q, int include_lgamma) {
     double t;
     if (s > 0.0) t = q > 0.0 ? s * log(q) - q : -INFINITY;
@@ -320,6 +325,14 @@ __global__ void __launch_bounds__(NT, (fused_min_blocks<N, NT>())) mlem_fused_ke
                 const float* XrT = Xc + NN;
                 const float* Uc = QUAD ? Xc + 2 * NN : Xc + NN;
                 const float* Ur = Uc + N;
+                {   // the next grid's exponent planes are read from DRAM
+                    // once per iteration: start that read now (one 128-byte
+                    // line per thread, 2 n^2 floats per grid)
+                    const int gn = gi + 1 < ngrid ? gi + 1 : 0;
+                    const float* nxt = tab + gn * gstride;
+                    constexpr int kLines = (int)((2 * (size_t)NN * sizeof(float) + 127) / 128);
+                    for (int l = tid; l < (QUAD ? kLines : kLines / 2); l += NT) prefetch_l2(nxt + 32 * l);
+                }
                 const int vc1 = gi, vc2 = gi + V / 2;           // column views
                 const int vr1 = gi + V / 4, vr2 = gi + 3 * V / 4;  // row views (QUAD)
                 // forward, column views: sample F on the grid
