@@ -318,6 +318,7 @@ def run_gpu(args, rank, world, local_rank):
     if rank != 0:
         return
     plain = None if args.no_plain else plain_timing(g, boac, mu, S_d, dev, stream, K)
+    grad = None if args.no_plain else grad_timing(g, t, boac, c_d, S_d, dev, stream)
 
     # ---- roofline of the dominant kernel (the fused MLEM kernel)
     kavg_s = sum(kern_ms) / len(kern_ms) / 1e3
@@ -358,6 +359,8 @@ def run_gpu(args, rank, world, local_rank):
     }
     if plain is not None:
         line["plain_path"] = dict(plain, speedup_of_batched=value / world / plain["value"])
+    if grad is not None:
+        line["differentiable_score"] = grad
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sample()
     print(json.dumps(line), flush=True)
@@ -397,6 +400,25 @@ def e2e_timing(args, world, dev, stream, step, c_d, S_d, L, F, coefs, S_np, flus
     return {"value": weak_scaling_value(world, B * K, args.steps, e_tot), "unit": UNIT,
             "h2d_bytes_per_step": c_h.numel() * 4 + S_h.numel() * 4,
             "d2h_bytes_per_step": L_h.numel() * 8 + F_h.numel() * 4}
+
+
+def grad_timing(g, t, boac, c_d, S_d, dev, stream):
+    """Score and d lnP / dc through unrolled MLEM (64 candidates, 10
+    iterations, checkpoint every 2): candidate-iterations per second."""
+    import torch
+    wl = synth.GRAD
+    E = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    c = c_d[:wl.B].contiguous()
+    boac.boac_score_grad(g, t, c, S_d, wl.K, wl.extra["ckpt_every"])
+    torch.cuda.synchronize(dev)
+    a, b = E(), E()
+    a.record(stream)
+    boac.boac_score_grad(g, t, c, S_d, wl.K, wl.extra["ckpt_every"])
+    b.record(stream)
+    b.synchronize()
+    return {"value": wl.B * wl.K / (a.elapsed_time(b) / 1e3), "unit": UNIT,
+            "sample": f"{wl.B} candidates x {wl.K} iterations, score + gradient, checkpoint every "
+                      f"{wl.extra['ckpt_every']}"}
 
 
 def plain_timing(g, boac, mu, S_d, dev, stream, K):

@@ -523,29 +523,33 @@ static const FusedVariant* get_variant(const boac_geom* g, int config) {
     return v;
 }
 
+// Resident CTAs per SM of a variant, computed for the largest view table it
+// may be launched with (the per-view table is a few KB, so this equals the
+// occupancy at every view count); cached per device.
 static int variant_occupancy(const FusedVariant* v, int V) {
     constexpr int kDev = 64;
-    static int cached[kDev][4][kConfigs][kMaxViews + 1];  // 0 = not yet computed
+    static int cached[kDev][4][kConfigs];  // 0 = not yet computed
     int dev = 0;
+    if (V < 0 || V > kMaxViews) return 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) {
         cudaGetLastError();
         return 0;
     }
     const int ni = v->n == 64 ? 0 : (v->n == 96 ? 1 : (v->n == 128 ? 2 : 3));
     const int ci = (int)(v - variant_table(v->n));
-    if (V < 0 || V > kMaxViews) return 0;
-    if (dev < kDev && cached[dev][ni][ci][V]) return cached[dev][ni][ci][V];
+    if (dev < kDev && cached[dev][ni][ci]) return cached[dev][ni][ci];
     if (cudaFuncSetAttribute(v->func, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)v->smem(kMaxViews)) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, v->func, v->nt, v->smem(V)) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, v->func, v->nt, v->smem(kMaxViews)) !=
+        cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
-    if (dev < kDev) cached[dev][ni][ci][V] = nb;
+    if (dev < kDev) cached[dev][ni][ci] = nb;
     return nb;
 }
 
