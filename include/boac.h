@@ -50,6 +50,8 @@ extern "C" {
 #define BOAC_ECUDA (-2)        /* a CUDA call or launch failed              */
 #define BOAC_EWORKSPACE (-3)   /* workspace missing or too small            */
 #define BOAC_EUNSUPPORTED (-4) /* valid geometry this build has no kernel for */
+#define BOAC_ETIMEOUT (-5)     /* a bounded wait on the device ran out (see
+                                  boac_workspace_status)                   */
 
 /* ---- types ------------------------------------------------------------- */
 /* Scanner geometry (see the discretisation above). */
@@ -85,6 +87,16 @@ const char *boac_status_string(int status);
 
 /* ABI version of this library (incremented on incompatible changes). */
 int boac_abi_version(void);
+
+/* Device status left in a boac_mlem / boac_mlem_ragged workspace by the last
+ * call that used it: BOAC_OK, or BOAC_ETIMEOUT if a kernel gave up one of its
+ * bounded waits (the affected candidates' scores are NaN and their images
+ * unspecified).  The fused kernel splits the batch's iterations evenly over
+ * its CTAs, so a candidate may be continued by a second CTA, which waits for
+ * a flag from the first; the schedule leaves that wait a whole candidate's
+ * worth of slack, and it gives up after about 8 s.  Synchronous: copies the
+ * word to *status after the device work queued before it has finished. */
+int boac_workspace_status(const void *ws, size_t ws_bytes, int *status);
 
 /* Bytes of device workspace that `op` needs for B candidates of geometry g
  * on the current device (0 if none).  For BOAC_OP_SCORE_GRAD the size also

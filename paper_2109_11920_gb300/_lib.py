@@ -20,6 +20,7 @@ BOAC_EINVAL = -1
 BOAC_ECUDA = -2
 BOAC_EWORKSPACE = -3
 BOAC_EUNSUPPORTED = -4
+BOAC_ETIMEOUT = -5
 
 RASTER_CENTER = 0
 RASTER_AREA = 1
@@ -77,6 +78,7 @@ _TP = ctypes.POINTER(Tissue)
 SIGNATURES = {
     "boac_status_string": (ctypes.c_char_p, [_I]),
     "boac_abi_version": (_I, []),
+    "boac_workspace_status": (_I, [_P, _SZ, ctypes.POINTER(ctypes.c_int)]),
     "boac_workspace_bytes": (_SZ, [_GP, _I, _I]),
     "boac_rasterize_mu": (_I, [_GP, _TP, _P, _I, _I, _P, _P]),
     "boac_project": (_I, [_GP, _P, _P, _I, _P, _P]),

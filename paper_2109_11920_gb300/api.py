@@ -58,6 +58,13 @@ def workspace(g: Geom, B: int, op: int, device) -> torch.Tensor | None:
     return torch.empty(nbytes, dtype=torch.uint8, device=device)
 
 
+def boac_workspace_status(ws: torch.Tensor) -> int:
+    """Device status word of a boac_mlem / ragged workspace (synchronous)."""
+    st = ctypes.c_int(0)
+    check("boac_workspace_status", _lib.load().boac_workspace_status(_ptr(ws), ws.numel(), ctypes.byref(st)))
+    return int(st.value)
+
+
 def boac_rasterize_mu(g: Geom, t: Tissue, c: torch.Tensor, mode: int = _lib.RASTER_CENTER,
                       out: torch.Tensor | None = None) -> torch.Tensor:
     """Eq. 3-4: mu[B, n, n] (cm^-1) from Legendre coefficients c[B, 6] (cm)."""

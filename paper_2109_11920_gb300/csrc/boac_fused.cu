@@ -60,12 +60,29 @@ struct FusedArgs {
     // and sample buffer live in a per-slot region of the workspace instead
     // (same layout), read through L1 and written through to L2.
     float* img;   // [slots][2 IMG + n WP] or unused
-    // Ragged batches: per-candidate records (device) and a work counter that
-    // CTAs advance with atomicAdd (largest K first, set up by the host).
+    // Ragged batches: per-candidate records (device), sorted by the host;
     // nullptr: uniform batch, candidate b at b * n^2 / b * s_stride, K = K.
     const RaggedDesc* desc;
-    int* counter;
+    // Work split.  The batch's iterations are laid end to end, candidate
+    // after candidate (candidate j occupies units [job_start[j],
+    // job_start[j+1]), max(K, 1) units each; job_start == nullptr for a
+    // uniform batch), and CTA m runs units [m cap, (m+1) cap) with
+    // cap >= the longest candidate (McNaughton's wrap-around rule: every CTA
+    // gets the same share, a candidate is cut between at most two CTAs).
+    // A CTA takes its candidates in descending order, so the first part of
+    // a cut candidate runs first on CTA m and its second part last on CTA
+    // m+1; ready[j] tells the second part that the first has written F
+    // (always long before it is needed, since cap >= the candidate length).
+    const long long* job_start;
+    long long cap;
+    int* ready;    // [B] zeroed before the launch
+    int* status;   // 0, or BOAC_ETIMEOUT if a bounded wait ran out
 };
+
+// Cycles a CTA waits for the first part of a cut candidate before giving up
+// (about 8 s at 2 GHz; the schedule leaves it a whole candidate's worth of
+// slack, so the wait ends immediately in practice).
+constexpr long long kReadySpinCycles = 1LL << 34;
 
 // Shared-memory and work layout of one CTA (image side N, NT threads).
 template <int N, int NT>
@@ -205,20 +222,37 @@ __global__ void __launch_bounds__(NT, (fused_min_blocks<N, NT>())) mlem_fused_ke
     float* tab = a.tab + (size_t)blockIdx.x * fused_tab_floats(N, V);
     float* sens = a.sens + (size_t)blockIdx.x * NN;
 
-    __shared__ int next_cand;
-    for (int cand = blockIdx.x;; cand += gridDim.x) {
-        if (a.desc) {  // ragged: take the next candidate from the queue
-            if (tid == 0) next_cand = atomicAdd(a.counter, 1);
-            __syncthreads();
-            cand = next_cand;
+    __shared__ int wait_ok;
+    const long long units = a.job_start ? a.job_start[a.B] : (long long)a.B * (a.K > 0 ? a.K : 1);
+    const long long m0 = (long long)blockIdx.x * a.cap;
+    const long long m1 = m0 + a.cap < units ? m0 + a.cap : units;
+    // candidate whose units contain x
+    auto job_of = [&](long long x) -> int {
+        if (!a.job_start) return (int)(x / (a.K > 0 ? a.K : 1));
+        int lo = 0, hi = a.B - 1;  // largest j with job_start[j] <= x
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (a.job_start[mid] <= x) lo = mid;
+            else hi = mid - 1;
         }
-        if (cand >= a.B) break;
+        return lo;
+    };
+    const int j_first = m0 < m1 ? job_of(m0) : 0;
+    const int j_last = m0 < m1 ? job_of(m1 - 1) : -1;
+
+    for (int cand = j_last; cand >= j_first; --cand) {
         const RaggedDesc* d = a.desc ? a.desc + cand : nullptr;
         const float* __restrict__ S = a.S + (d ? d->S_off : (long long)cand * a.s_stride);
         const float* __restrict__ mu = a.mu + (d ? d->mu_off : (long long)cand * NN);
         float* Fc = a.F + (d ? d->F_off : (long long)cand * NN);
         const int Kc = d ? d->K : a.K;
         const int lidx = d ? d->out : cand;
+        // this CTA's part of the candidate: iterations [it0, it1)
+        const long long js = a.job_start ? a.job_start[cand] : (long long)cand * (a.K > 0 ? a.K : 1);
+        const long long jl = Kc > 0 ? Kc : 1;
+        const long long u0 = m0 - js > 0 ? m0 - js : 0, u1 = m1 - js < jl ? m1 - js : jl;
+        const bool first = (u0 == 0), last = (u1 == jl);
+        const int it0 = (int)(u0 < Kc ? u0 : Kc), it1 = (int)(u1 < Kc ? u1 : Kc);
 
         // ---- set-up: mu -> img0 (zero ring), img1 = 0
         for (int i = tid; i < IMG; i += NT) {
@@ -305,10 +339,34 @@ __global__ void __launch_bounds__(NT, (fused_min_blocks<N, NT>())) mlem_fused_ke
             __syncthreads();
             scatter_classes<N, NT>(W, img1, cs, sn, c);
         }
+        if (tid == 0) {  // second part of a cut candidate: wait for the first
+            int ok = 1;
+            if (!first) {
+                const long long t0 = clock64();
+                for (;;) {
+                    int f;
+                    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(f) : "l"(a.ready + cand) : "memory");
+                    if (f) break;
+                    if (clock64() - t0 > kReadySpinCycles) {
+                        ok = 0;
+                        atomicExch(a.status, BOAC_ETIMEOUT);
+                        break;
+                    }
+                    __nanosleep(256);
+                }
+            }
+            wait_ok = ok;
+        }
+        __syncthreads();
+        if (!wait_ok) {  // give up on this part: no F written, score NaN
+            if (tid == 0 && last && a.L) a.L[lidx] = __longlong_as_double(0x7ff8000000000000LL);
+            __syncthreads();
+            continue;
+        }
         for (int i = tid; i < NN; i += NT) {
             const int pi = (i / N + 1) * P + (i % N) + 1;
             sens[i] = img1[pi];
-            img0[pi] = Fc[i];
+            img0[pi] = first ? Fc[i] : __ldcg(Fc + i);  // L2: written by another SM
         }
         __syncthreads();
         for (int i = tid; i < IMG; i += NT) img1[i] = 0.0f;
@@ -316,9 +374,9 @@ __global__ void __launch_bounds__(NT, (fused_min_blocks<N, NT>())) mlem_fused_ke
 
         // ---- MLEM iterations, then one more forward pass for the score
         double lacc = 0.0;
-        for (int it = 0; it <= Kc; ++it) {
+        for (int it = it0; it <= it1; ++it) {
             const bool scoring = (it == Kc);
-            if (scoring && !a.L) break;
+            if (it == it1 && !(last && a.L)) break;
             for (int gi = 0; gi < ngrid; ++gi) {
                 const float cs = csn[2 * gi], sn = csn[2 * gi + 1];
                 const float* Xc = tab + gi * gstride;
@@ -429,7 +487,7 @@ __global__ void __launch_bounds__(NT, (fused_min_blocks<N, NT>())) mlem_fused_ke
         }
 
         // ---- Eq. 5: deterministic block reduction of the float64 terms
-        if (a.L) {
+        if (last && a.L) {
             for (int off = 16; off > 0; off >>= 1) lacc += __shfl_down_sync(0xffffffffu, lacc, off);
             if ((tid & 31) == 0) dred[tid >> 5] = lacc;
             __syncthreads();
@@ -440,9 +498,13 @@ __global__ void __launch_bounds__(NT, (fused_min_blocks<N, NT>())) mlem_fused_ke
             }
         }
 
-        // ---- F^K out
+        // ---- F out (F^K, or the state handed to the candidate's second part)
         for (int i = tid; i < NN; i += NT) Fc[i] = img0[(i / N + 1) * P + (i % N) + 1];
         __syncthreads();
+        if (!last && tid == 0) {
+            __threadfence();
+            asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(a.ready + cand), "r"(1) : "memory");
+        }
     }
 }
 
@@ -553,21 +615,30 @@ static int variant_occupancy(const FusedVariant* v, int V) {
     return nb;
 }
 
-// Workspace for `slots` CTA slots: the attenuation-exponent tables, then the
-// sensitivity images.  Returns the total bytes; *sens_off the offset of the
-// sensitivity images.
-static size_t fused_slot_layout(const boac_geom* g, int slots, size_t* sens_off = nullptr,
-                                size_t* img_off = nullptr) {
-    const size_t tab = align256(sizeof(float) * (size_t)slots * fused_tab_floats(g->n, g->n_views));
-    const size_t sens = align256(sizeof(float) * (size_t)slots * g->n * g->n);
-    if (sens_off) *sens_off = tab;
-    if (img_off) *img_off = tab + sens;
+// Workspace of the fused kernel for `slots` CTA slots and B candidates:
+//   [0, 256)   status word (BOAC_OK, or BOAC_ETIMEOUT from a bounded wait)
+//   tables     attenuation exponents, one region per slot
+//   sens       sensitivity image per slot
+//   images     padded F / accumulator / sample buffer per slot (n > 128)
+//   ready      one flag per candidate (the work split's hand-over)
+struct FusedLayout {
+    size_t status, tab, sens, img, ready, total;
+};
+
+static FusedLayout fused_layout(const boac_geom* g, int slots, int B) {
+    FusedLayout l;
+    l.status = 0;
+    l.tab = 256;
+    l.sens = l.tab + align256(sizeof(float) * (size_t)slots * fused_tab_floats(g->n, g->n_views));
+    l.img = l.sens + align256(sizeof(float) * (size_t)slots * g->n * g->n);
     // padded F and accumulator, (n+1)(n+2)+1 floats each, and the n x (n+1)
     // sample buffer, for sides held in global memory
     const size_t img_floats = fused_global_images(g->n)
                                   ? 2 * ((size_t)(g->n + 1) * (g->n + 2) + 1) + (size_t)g->n * (g->n + 1)
                                   : 0;
-    return tab + sens + align256(sizeof(float) * (size_t)slots * img_floats);
+    l.ready = l.img + align256(sizeof(float) * (size_t)slots * img_floats);
+    l.total = l.ready + align256(sizeof(int) * (size_t)B);
+    return l;
 }
 
 static int variant_slots(const boac_geom* g, const FusedVariant* v, int B) {
@@ -584,12 +655,19 @@ int fused_slots(const boac_geom* g, int B) {
 
 size_t fused_workspace_bytes(const boac_geom* g, int B) {
     const int slots = fused_slots(g, B);
-    return slots > 0 ? fused_slot_layout(g, slots) : 0;
+    return slots > 0 ? fused_layout(g, slots, B).total : 0;
 }
 
-static FusedArgs uniform_args(const boac_geom* g, const float* mu, const float* S, long long s_stride,
-                              float* F, int K, int B, double* L, int include_lgamma, void* scratch,
-                              int slots) {
+// Units per CTA of the work split: the larger of an even share and the
+// longest candidate (so that a candidate is never cut into three parts).
+static long long split_cap(long long units, long long longest, int slots) {
+    const long long share = (units + slots - 1) / slots;
+    return share > longest ? share : longest;
+}
+
+static FusedArgs base_args(const boac_geom* g, const float* mu, const float* S, long long s_stride,
+                           float* F, int K, int B, double* L, int include_lgamma, char* ws,
+                           const FusedLayout& l) {
     FusedArgs a;
     a.mu = mu;
     a.S = S;
@@ -601,22 +679,43 @@ static FusedArgs uniform_args(const boac_geom* g, const float* mu, const float* 
     a.V = g->n_views;
     a.K = K;
     a.dx = g->pixel_cm;
-    size_t sens_off = 0, img_off = 0;
-    fused_slot_layout(g, slots, &sens_off, &img_off);
-    a.tab = static_cast<float*>(scratch);
-    a.sens = reinterpret_cast<float*>(static_cast<char*>(scratch) + sens_off);
-    a.img = reinterpret_cast<float*>(static_cast<char*>(scratch) + img_off);
+    a.tab = reinterpret_cast<float*>(ws + l.tab);
+    a.sens = reinterpret_cast<float*>(ws + l.sens);
+    a.img = reinterpret_cast<float*>(ws + l.img);
     a.desc = nullptr;
-    a.counter = nullptr;
+    a.job_start = nullptr;
+    a.cap = 0;
+    a.ready = reinterpret_cast<int*>(ws + l.ready);
+    a.status = reinterpret_cast<int*>(ws + l.status);
     return a;
 }
 
+// Uniform batch: zero the status and ready flags, then launch the CTAs that
+// have work under the split.
+static int launch_uniform(const boac_geom* g, const FusedVariant* v, int slots, const float* mu,
+                          const float* S, long long s_stride, float* F, int K, int B, double* L,
+                          int include_lgamma, char* ws, cudaStream_t st) {
+    const FusedLayout l = fused_layout(g, slots, B);
+    FusedArgs a = base_args(g, mu, S, s_stride, F, K, B, L, include_lgamma, ws, l);
+    const long long per = K > 0 ? K : 1, units = (long long)B * per;
+    a.cap = split_cap(units, per, slots);
+    const int grid = (int)((units + a.cap - 1) / a.cap);
+    if (cudaMemsetAsync(ws + l.status, 0, sizeof(int), st) != cudaSuccess ||
+        cudaMemsetAsync(ws + l.ready, 0, sizeof(int) * (size_t)B, st) != cudaSuccess)
+        return launch_status();
+    return v->launch(a, grid, st);
+}
+
 // ---------------------------------------------------------------- ragged
+// Ragged workspace: [0, 256) status word; per class: the candidates'
+// records, their unit offsets (job_start, B_c + 1 values) and the class's
+// fused layout (without its own status word).
 struct RaggedPlan {
     int cls_count[kMaxRaggedClasses];
     int slots[kMaxRaggedClasses];
     const FusedVariant* var[kMaxRaggedClasses];
-    size_t desc_off[kMaxRaggedClasses], tab_off[kMaxRaggedClasses], counter_off, total;
+    size_t desc_off[kMaxRaggedClasses], start_off[kMaxRaggedClasses], layout_off[kMaxRaggedClasses];
+    size_t total;
 };
 
 static int ragged_plan(const boac_geom* classes, int n_classes, const boac_ragged_cand* cands, int B,
@@ -632,23 +731,36 @@ static int ragged_plan(const boac_geom* classes, int n_classes, const boac_ragge
             return BOAC_EINVAL;
         pl->cls_count[d.cls]++;
     }
-    size_t off = 0;
+    size_t off = 256;
     for (int c = 0; c < n_classes; ++c) {
         if (!variant_table(classes[c].n)) return BOAC_EUNSUPPORTED;
         const int cfg = config ? config[c] : default_config(&classes[c]);
         pl->var[c] = get_variant(&classes[c], cfg);
         if (!pl->var[c]) return BOAC_EINVAL;
-        pl->slots[c] = pl->cls_count[c] ? variant_slots(&classes[c], pl->var[c], pl->cls_count[c]) : 0;
-        if (pl->cls_count[c] && pl->slots[c] <= 0) return BOAC_ECUDA;
+        const int cnt = pl->cls_count[c];
+        pl->slots[c] = cnt ? variant_slots(&classes[c], pl->var[c], cnt) : 0;
+        if (cnt && pl->slots[c] <= 0) return BOAC_ECUDA;
         pl->desc_off[c] = off;
-        off += align256(sizeof(RaggedDesc) * (size_t)pl->cls_count[c]);
-        pl->tab_off[c] = off;
-        off += pl->slots[c] ? fused_slot_layout(&classes[c], pl->slots[c]) : 0;
+        off += align256(sizeof(RaggedDesc) * (size_t)cnt);
+        pl->start_off[c] = off;
+        off += align256(sizeof(long long) * ((size_t)cnt + 1));
+        pl->layout_off[c] = off;
+        off += cnt ? fused_layout(&classes[c], pl->slots[c], cnt).total : 0;
     }
-    pl->counter_off = off;
-    off += align256(sizeof(int) * kMaxRaggedClasses);
     pl->total = off;
     return BOAC_OK;
+}
+
+// The candidates in the order the kernels process them: by class, then by
+// decreasing K.
+static std::vector<int> ragged_order(const boac_ragged_cand* cands, int B) {
+    std::vector<int> order((size_t)B);
+    for (int b = 0; b < B; ++b) order[b] = b;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        if (cands[x].cls != cands[y].cls) return cands[x].cls < cands[y].cls;
+        return cands[x].K > cands[y].K;
+    });
+    return order;
 }
 
 }  // namespace boac
@@ -664,9 +776,15 @@ extern "C" int boac_mlem(const boac_geom* g, const float* mu, const float* S, lo
     if (!v) return BOAC_EUNSUPPORTED;
     const int slots = variant_slots(g, v, B);
     if (slots <= 0) return BOAC_ECUDA;
-    if (!ws || ws_bytes < fused_slot_layout(g, slots)) return BOAC_EWORKSPACE;
-    const FusedArgs a = uniform_args(g, mu, S, s_stride, F, K, B, L, include_lgamma, ws, slots);
-    return v->launch(a, slots, as_stream(stream));
+    if (!ws || ws_bytes < fused_layout(g, slots, B).total) return BOAC_EWORKSPACE;
+    return launch_uniform(g, v, slots, mu, S, s_stride, F, K, B, L, include_lgamma,
+                          static_cast<char*>(ws), as_stream(stream));
+}
+
+extern "C" int boac_workspace_status(const void* ws, size_t ws_bytes, int* status) {
+    if (!ws || ws_bytes < sizeof(int) || !status) return BOAC_EINVAL;
+    if (cudaMemcpy(status, ws, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return launch_status();
+    return BOAC_OK;
 }
 
 extern "C" size_t boac_mlem_ragged_workspace_bytes(const boac_geom* classes, int n_classes,
@@ -683,26 +801,26 @@ extern "C" int boac_mlem_ragged_prepare(const boac_geom* classes, int n_classes,
     int s = ragged_plan(classes, n_classes, cands, B, config, &pl);
     if (s != BOAC_OK) return s;
     if (!ws || ws_bytes < pl.total) return BOAC_EWORKSPACE;
-    // Per-class records, largest K first (longest-processing-time order for
-    // the CTAs' shared work queue).  Copied from pageable host memory, so
-    // the copy is staged before this call returns.
-    std::vector<RaggedDesc> host((size_t)B);
-    std::vector<int> order((size_t)B);
-    for (int b = 0; b < B; ++b) order[b] = b;
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-        if (cands[x].cls != cands[y].cls) return cands[x].cls < cands[y].cls;
-        return cands[x].K > cands[y].K;
-    });
-    for (int i = 0; i < B; ++i) {
-        const boac_ragged_cand& d = cands[order[i]];
-        host[i] = RaggedDesc{d.mu_off, d.S_off, d.F_off, d.K, order[i]};
-    }
+    // Per-class records and unit offsets, copied from pageable host memory
+    // (the copies are staged before this call returns).
+    const std::vector<int> order = ragged_order(cands, B);
+    std::vector<RaggedDesc> desc((size_t)B);
+    std::vector<long long> start((size_t)B + n_classes);
     char* base = static_cast<char*>(ws);
     int first = 0;
     for (int c = 0; c < n_classes; ++c) {
         const int cnt = pl.cls_count[c];
         if (cnt == 0) continue;
-        if (cudaMemcpyAsync(base + pl.desc_off[c], host.data() + first, sizeof(RaggedDesc) * cnt,
+        long long* js = start.data() + first + c;
+        js[0] = 0;
+        for (int i = 0; i < cnt; ++i) {
+            const boac_ragged_cand& d = cands[order[first + i]];
+            desc[first + i] = RaggedDesc{d.mu_off, d.S_off, d.F_off, d.K, order[first + i]};
+            js[i + 1] = js[i] + (d.K > 0 ? d.K : 1);
+        }
+        if (cudaMemcpyAsync(base + pl.desc_off[c], desc.data() + first, sizeof(RaggedDesc) * cnt,
+                            cudaMemcpyHostToDevice, as_stream(stream)) != cudaSuccess ||
+            cudaMemcpyAsync(base + pl.start_off[c], js, sizeof(long long) * (cnt + 1),
                             cudaMemcpyHostToDevice, as_stream(stream)) != cudaSuccess)
             return launch_status();
         first += cnt;
@@ -721,16 +839,28 @@ extern "C" int boac_mlem_ragged_run(const boac_geom* classes, int n_classes,
     if (!ws || ws_bytes < pl.total) return BOAC_EWORKSPACE;
     char* base = static_cast<char*>(ws);
     cudaStream_t st = as_stream(stream);
-    if (cudaMemsetAsync(base + pl.counter_off, 0, sizeof(int) * kMaxRaggedClasses, st) != cudaSuccess)
-        return launch_status();
+    if (cudaMemsetAsync(base, 0, sizeof(int), st) != cudaSuccess) return launch_status();
+    // units and longest candidate per class (the same order as prepare's)
+    long long units[kMaxRaggedClasses] = {0}, longest[kMaxRaggedClasses] = {0};
+    for (int b = 0; b < B; ++b) {
+        const long long len = cands[b].K > 0 ? cands[b].K : 1;
+        units[cands[b].cls] += len;
+        if (len > longest[cands[b].cls]) longest[cands[b].cls] = len;
+    }
     for (int c = 0; c < n_classes; ++c) {
         const int cnt = pl.cls_count[c];
         if (cnt == 0) continue;
-        FusedArgs a = uniform_args(&classes[c], mu_pool, S_pool, 0, F_pool, 0, cnt, L, include_lgamma,
-                                   base + pl.tab_off[c], pl.slots[c]);
+        const FusedLayout l = fused_layout(&classes[c], pl.slots[c], cnt);
+        char* cbase = base + pl.layout_off[c];
+        FusedArgs a = base_args(&classes[c], mu_pool, S_pool, 0, F_pool, 0, cnt, L, include_lgamma, cbase, l);
         a.desc = reinterpret_cast<const RaggedDesc*>(base + pl.desc_off[c]);
-        a.counter = reinterpret_cast<int*>(base + pl.counter_off) + c;
-        s = pl.var[c]->launch(a, pl.slots[c], st);
+        a.job_start = reinterpret_cast<const long long*>(base + pl.start_off[c]);
+        a.status = reinterpret_cast<int*>(base);  // one status word for the call
+        a.cap = split_cap(units[c], longest[c], pl.slots[c]);
+        const int grid = (int)((units[c] + a.cap - 1) / a.cap);
+        if (cudaMemsetAsync(cbase + l.ready, 0, sizeof(int) * (size_t)cnt, st) != cudaSuccess)
+            return launch_status();
+        s = pl.var[c]->launch(a, grid, st);
         if (s != BOAC_OK) return s;
     }
     return BOAC_OK;
@@ -787,11 +917,12 @@ static void* noalloc_scratch_ptr() {
     return cached[dev];
 }
 
-// Largest number of resident CTA slots whose tables and sensitivity images
-// fit the built-in scratch (0 if not even one does).
+// Largest number of resident CTA slots whose tables, sensitivity images and
+// the candidates' hand-over flags fit the built-in scratch (0 if not even
+// one slot does).
 static int noalloc_slots(const boac_geom* g, int B) {
     int slots = fused_slots(g, B);
-    while (slots > 0 && fused_slot_layout(g, slots) > kNoAllocScratchBytes) --slots;
+    while (slots > 0 && fused_layout(g, slots, B).total > kNoAllocScratchBytes) --slots;
     return slots;
 }
 
@@ -810,7 +941,8 @@ extern "C" int boac_mlem_noalloc(const boac_geom* g, const float* mu, const floa
     void* scratch = noalloc_scratch_ptr();
     if (!scratch) return BOAC_ECUDA;
     // The kernel writes every table entry and sensitivity pixel of a slot
-    // before reading it, so the scratch needs no clearing between calls.
-    const FusedArgs a = uniform_args(g, mu, S, s_stride, F, K, B, L, include_lgamma, scratch, slots);
-    return v->launch(a, slots, as_stream(stream));
+    // before reading it; the status word and the candidates' hand-over flags
+    // must start at zero and are cleared here, on the caller's stream.
+    return launch_uniform(g, v, slots, mu, S, s_stride, F, K, B, L, include_lgamma,
+                          static_cast<char*>(scratch), as_stream(stream));
 }

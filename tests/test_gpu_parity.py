@@ -176,16 +176,35 @@ def test_edge_cases(cuda, probs):
 
 def test_mlem_batched_full_size_sampled(cuda):
     """The batched workload at full size (128^2, 120 views, 256 candidates,
-    50 iterations, one launch as the benchmark times it); candidates from the
-    first and second pass of the persistent grid and the last one checked
-    against the oracle."""
+    50 iterations, one launch as the benchmark times it); the first candidate,
+    candidates cut between two CTAs by the work split (1, 152) and the last
+    one checked against the oracle."""
     wl = synth.BATCHED
     p = make_problem(wl.n, wl.dx, wl.V, wl.counts, B=wl.B, seed=wl.seed)
     F, L = run_mlem(p, cuda, wl.K, plain=False)
-    nsm = torch.cuda.get_device_properties(cuda).multi_processor_count
-    picks = sorted({0, min(nsm, wl.B - 1), wl.B - 1})
+    picks = [0, 1, 152, wl.B - 1]
     Fo, Lo, _ = oracle.mlem_batch(p.geom, p.mu[picks], p.S, wl.K)
     for i, b in enumerate(picks):
         assert rel_l2(F[b], Fo[i]) < 1e-4, b
         assert abs(L[b] - Lo[i]) < 1e-6 * abs(Lo[i]), b
     assert np.all(np.isfinite(L)) and np.all(F >= 0)
+
+
+def test_work_split_status_and_odd_batches(cuda, probs):
+    """The fused kernel splits a batch's iterations evenly over its CTAs and
+    may cut a candidate between two of them; batches of every size give the
+    same images as one-candidate calls, and the workspace status stays OK."""
+    p = probs[SHAPES[0]]
+    g = geom(p)
+    mu1 = T(p.mu[:1], cuda)
+    S = T(p.S, cuda)
+    F1 = torch.ones(1, p.n, p.n, device=cuda)
+    F1, L1 = boac.boac_mlem(g, mu1, S, F1, 7)
+    for B in (2, 5, 151, 152, 153, 457):
+        mu = mu1.expand(B, p.n, p.n).contiguous()
+        ws = boac.workspace(g, B, boac._lib.OP_MLEM, cuda)
+        F = torch.ones(B, p.n, p.n, device=cuda)
+        F, L = boac.boac_mlem(g, mu, S, F, 7, ws=ws)
+        assert boac.boac_workspace_status(ws) == boac._lib.BOAC_OK
+        torch.testing.assert_close(F, F1.expand(B, p.n, p.n), rtol=0, atol=0)
+        torch.testing.assert_close(L, L1.expand(B), rtol=0, atol=0)
