@@ -234,8 +234,10 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline_sample():
-    """The oracle as it stands, timed on this host's cores (bounded sample)."""
+def cpu_baseline_sample(dev=None):
+    """The oracle as it stands, timed on this host's cores (bounded sample);
+    the same candidates through the CUDA path give its error against the
+    oracle (images after the full iteration count, scores)."""
     import oracle
     sys.path.insert(0, os.path.join(ROOT, "tests"))
     from problems import make_problem
@@ -244,12 +246,26 @@ def cpu_baseline_sample():
     B = 4 * cores
     p = make_problem(WL.n, WL.dx, WL.V, WL.counts, B=B, seed=WL.seed)
     t0 = time.perf_counter()
-    _, _, used = oracle.mlem_batch(p.geom, p.mu, p.S, K, with_score=True, nthreads=cores)
+    Fo, Lo, used = oracle.mlem_batch(p.geom, p.mu, p.S, K, with_score=True, nthreads=cores)
     dt = time.perf_counter() - t0
-    return {"value": B * K / dt, "unit": UNIT, "cores": used, "kind": "oracle",
-            "sample": f"{B} candidates x {K} MLEM iterations + score of the "
-                      f"{WL.n}x{WL.n}/{WL.V}-view batch (FP64 C, candidates spread over "
-                      f"{used} threads), {dt:.1f} s wall"}
+    out = {"value": B * K / dt, "unit": UNIT, "cores": used, "kind": "oracle",
+           "sample": f"{B} candidates x {K} MLEM iterations + score of the "
+                     f"{WL.n}x{WL.n}/{WL.V}-view batch (FP64 C, candidates spread over "
+                     f"{used} threads), {dt:.1f} s wall"}
+    if dev is not None:
+        import torch
+        from paper_2109_11920_gb300 import Geom
+        from paper_2109_11920_gb300 import api as boac
+        g = Geom.make(p.n, p.dx, p.V)
+        F = torch.ones(B, p.n, p.n, device=dev)
+        F, L = boac.boac_mlem(g, torch.tensor(p.mu, dtype=torch.float32, device=dev),
+                              torch.tensor(p.S, dtype=torch.float32, device=dev), F, K)
+        F, L = F.double().cpu().numpy(), L.cpu().numpy()
+        img = [float(np.linalg.norm(F[b] - Fo[b]) / np.linalg.norm(Fo[b])) for b in range(B)]
+        out["error_vs_oracle"] = {"image_rel_l2_max": max(img),
+                                  "score_rel_max": float(np.max(np.abs(L - Lo) / np.abs(Lo))),
+                                  "candidates": B, "iterations": K}
+    return out
 
 
 # ----------------------------------------------------------------- GPU arm
@@ -362,7 +378,7 @@ def run_gpu(args, rank, world, local_rank):
     if grad is not None:
         line["differentiable_score"] = grad
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_sample()
+        line["cpu_baseline"] = cpu_baseline_sample(dev)
     print(json.dumps(line), flush=True)
 
 
@@ -441,6 +457,133 @@ def plain_timing(g, boac, mu, S_d, dev, stream, K):
             "sample": f"{nplain} candidates x {K} iterations, 4 launches per iteration"}
 
 
+# ----------------------------------------------------------------- other workloads
+def _timed(fn, dev, reps=2):
+    """Best of `reps` CUDA-event timings of fn() after one warm-up call (ms)."""
+    import torch
+    fn()
+    torch.cuda.synchronize(dev)
+    best = float("inf")
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(torch.cuda.current_stream(dev))
+        fn()
+        b.record(torch.cuda.current_stream(dev))
+        b.synchronize()
+        best = min(best, a.elapsed_time(b))
+    return best
+
+
+def _phantom_sinograms(boac, Geom, Tissue, dev, n, dx, V, counts, seeds, c_true=None):
+    """Seeded phantoms and Poisson sinograms built on the device, one per seed."""
+    import torch
+    g = Geom.make(n, dx, V)
+    t = Tissue(*synth.TISSUE)
+    out = []
+    for s in seeds:
+        ph, noise, _ = synth.streams(int(s))
+        ct = synth.C_TRUE if c_true is None else c_true[int(s) % len(c_true)]
+        mu_t = boac.boac_rasterize_mu(g, t, torch.tensor([ct], dtype=torch.float32, device=dev))
+        brain = (mu_t[0] == np.float32(synth.TISSUE[0])).cpu().numpy()
+        Ft = synth.paint_activity(n, float(np.float32(dx)), brain, synth.ellipses(ph, ct[0]))
+        q = boac.boac_project(g, mu_t, torch.tensor(Ft[None], dtype=torch.float32, device=dev))
+        out.append(torch.tensor(synth.poisson_sinogram(noise, q[0].double().cpu().numpy(), counts),
+                                dtype=torch.float32, device=dev))
+    return g, t, out
+
+
+def run_workload(args):
+    """Throughput of the other workloads of the hot path on one GPU (one JSON
+    line each): the single-candidate case, the ragged batch, the large slices
+    and the differentiable score."""
+    import torch
+    from paper_2109_11920_gb300 import Geom, Tissue
+    from paper_2109_11920_gb300 import api as boac
+    from paper_2109_11920_gb300 import autotune
+    from paper_2109_11920_gb300 import build as pkg_build
+    pkg_build.build()
+    dev = torch.device("cuda", 0)
+    peak = fp32_peak_tflops()
+    name = args.workload
+    if name == "small":
+        wl = synth.SMALL
+        g, t, (S,) = _phantom_sinograms(boac, Geom, Tissue, dev, wl.n, wl.dx, wl.V, wl.counts, [wl.seed])
+        c = torch.tensor(synth.candidates(synth.streams(wl.seed)[2], 1).astype(np.float32), device=dev)
+        mu = boac.boac_rasterize_mu(g, t, c)
+        F = torch.ones(1, wl.n, wl.n, device=dev)
+        ms = _timed(lambda: boac.boac_mlem(g, mu, S, F.fill_(1.0), wl.K), dev)
+        msp = _timed(lambda: boac.boac_mlem(g, mu, S, F.fill_(1.0), wl.K, plain=True), dev)
+        work = [(wl.V, wl.n, wl.K)]
+        extra = {"plain_path_ms": msp}
+        desc = f"{wl.name}: 1 candidate x {wl.K} iterations, {wl.n}x{wl.n}, {wl.V} views"
+    elif name in ("ragged", "large"):
+        if name == "ragged":
+            wl = synth.RAGGED
+            _, _, rng = synth.streams(wl.seed)
+            cls, K = synth.ragged_schedule(rng, wl.B, wl.extra["mix"], wl.extra["k_range"])
+            classes = wl.extra["classes"]
+            mus, Ss, geoms = [], [], []
+            for ci, (n, dx, V) in enumerate(classes):
+                members = [b for b in range(wl.B) if cls[b] == ci]
+                g, t, S_list = _phantom_sinograms(boac, Geom, Tissue, dev, n, dx, V, 2e5, [1000 + b for b in members])
+                geoms.append(g)
+                cc = torch.tensor(np.stack([synth.candidates(synth.streams(1000 + b)[2], 1)[0]
+                                            for b in members]).astype(np.float32), device=dev)
+                mu_c = boac.boac_rasterize_mu(g, t, cc)
+                for i, b in enumerate(members):
+                    mus.append((b, mu_c[i]))
+                    Ss.append((b, S_list[i]))
+            mus = [m for _, m in sorted(mus, key=lambda x: x[0])]
+            Ss = [x for _, x in sorted(Ss, key=lambda x: x[0])]
+            batch = boac.RaggedBatch(geoms, [int(x) for x in cls], [int(k) for k in K], mus, Ss, device=dev)
+            work = [(classes[int(cls[b])][2], classes[int(cls[b])][0], int(K[b])) for b in range(wl.B)]
+            desc = (f"{wl.name}: {wl.B} candidates, 64^2/60v : 96^2/90v : 128^2/120v = 1:1:2, "
+                    f"K ~ U{{20..80}}, own phantom per candidate")
+        else:
+            wl = synth.LARGE
+            n_sl, per = wl.extra["slices"], wl.B
+            c_sl = synth.slice_coefficients(np.random.default_rng(wl.seed), n_sl)
+            g, t, S_list = _phantom_sinograms(boac, Geom, Tissue, dev, wl.n, wl.dx, wl.V, wl.counts,
+                                              list(range(n_sl)), c_true=c_sl)
+            mus, Ss = [], []
+            for s in range(n_sl):
+                cc = torch.tensor(synth.candidates(synth.streams(s)[2], per, c_sl[s]).astype(np.float32), device=dev)
+                mu_c = boac.boac_rasterize_mu(g, t, cc)
+                mus += list(mu_c)
+                Ss += [S_list[s]] * per
+            batch = boac.RaggedBatch([g], [0] * (n_sl * per), [wl.K] * (n_sl * per), mus, Ss, device=dev)
+            work = [(wl.V, wl.n, wl.K)] * (n_sl * per)
+            desc = f"{wl.name}: {n_sl} slices x {per} candidates, 256x256, 180 views, K={wl.K}"
+        config = autotune.tune_ragged(batch, probe_iters=2, repeats=1) if not args.no_tune else None
+        batch.prepare(config)
+        ms = _timed(lambda: (batch.F_pool.fill_(1.0), batch.run()), dev, reps=1 if name == "large" else 2)
+        extra = {"launch_config": config}
+    elif name == "grad":
+        wl = synth.GRAD
+        g, t, (S,) = _phantom_sinograms(boac, Geom, Tissue, dev, wl.n, wl.dx, wl.V, wl.counts, [wl.seed])
+        c = torch.tensor(synth.candidates(synth.streams(wl.seed)[2], wl.B).astype(np.float32), device=dev)
+        ck = wl.extra["ckpt_every"]
+        ms = _timed(lambda: boac.boac_score_grad(g, t, c, S, wl.K, ck), dev)
+        # forward MLEM, recomputation of each checkpoint segment, and the
+        # adjoint iteration (two projections, two back-projections, the
+        # attenuation adjoint): about 4 MLEM iterations of work per iteration
+        work = [(wl.V, wl.n, 4 * wl.K)] * wl.B
+        extra = {"work_model_note": "4 MLEM-iteration equivalents per differentiated iteration"}
+        desc = f"{wl.name}: {wl.B} candidates, d lnP/dc through {wl.K} iterations, checkpoint every {ck}"
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    cand_its = sum(k for _, _, k in work) if name != "grad" else wl.B * wl.K
+    flops = sum(FLOPS_PER_SAMPLE * V * n * n * k for V, n, k in work)
+    line = {"metric": f"MLEM candidate-iterations/sec ({name} workload)", "value": cand_its / (ms / 1e3),
+            "unit": UNIT, "n_gpus": 1, "ms": ms, "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": desc},
+            "roofline": {"bound": "alu", "achieved": flops / (ms / 1e3) / 1e12, "peak": peak,
+                         "unit": "TFLOP/s", "frac": flops / (ms / 1e3) / 1e12 / peak,
+                         "work_model": f"{FLOPS_PER_SAMPLE} FP32 ops per ray sample per view per iteration"}}
+    line.update(extra)
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -453,7 +596,13 @@ def main():
     ap.add_argument("--iters", type=int, default=WL.K, help="MLEM iterations")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-path comparison")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffer) timing")
+    ap.add_argument("--workload", default="batched", choices=["batched", "small", "ragged", "large", "grad"],
+                    help="batched: the benchmark; the others print their own throughput line")
+    ap.add_argument("--no-tune", action="store_true", help="ragged/large: default launch shapes")
     args = ap.parse_args()
+    if args.workload != "batched":
+        run_workload(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

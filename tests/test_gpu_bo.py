@@ -1,0 +1,33 @@
+"""The BO driver on the GPU objective: a few batched cycles on a small
+problem improve the likelihood over the initial random set and move c_0 (the
+head size) towards the true value; the objective equals -L of boac_mlem."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2109_11920_gb300 import Geom, Tissue, bo, synth
+from paper_2109_11920_gb300 import api as boac
+from problems import make_problem
+
+pytestmark = pytest.mark.gpu
+
+
+def test_bo_driver_on_gpu_objective(cuda):
+    p = make_problem(64, 0.4, 60, 2e5, B=1, seed=31)
+    g, t = Geom.make(p.n, p.dx, p.V), Tissue(*p.tissue)
+    S = torch.tensor(p.S, dtype=torch.float32, device=cuda)
+    K = 8
+    evaluate = bo.gpu_objective(g, t, S, K, include_lgamma=False)
+    c_true = np.array(synth.C_TRUE)
+    # consistency with the library call
+    C = np.stack([c_true, c_true + 0.2])
+    mu = boac.boac_rasterize_mu(g, t, torch.tensor(C, dtype=torch.float32, device=cuda))
+    _, L = boac.boac_mlem(g, mu, S, torch.ones(2, p.n, p.n, device=cuda), K, include_lgamma=False)
+    np.testing.assert_allclose(evaluate(C), -L.cpu().numpy(), rtol=0, atol=0)
+    # search c_0 in [6.5, 9.5] cm, the shape terms around their true values
+    half = np.array([1.5, 0.15, 0.2, 0.1, 0.05, 0.03])
+    lo, hi = c_true - half, c_true + half
+    res = bo.BOACOptimizer(evaluate, lo, hi, batch=16, init=32, max_cycles=4, ei_threshold=0.0, seed=7).run()
+    init_f = res.history_f[:32]
+    assert res.best_f < np.min(init_f) or res.best_f <= np.percentile(init_f, 5)
+    assert abs(res.best_c[0] - c_true[0]) < np.median(np.abs(res.history_c[:32, 0] - c_true[0]))
