@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include "boac_internal.h"
+#include "boac_plain_kernels.cuh"
 
 namespace boac {
 
@@ -39,11 +40,17 @@ int launch_status() {
 }
 
 // Plain path workspace for one candidate at a time: attenuation table, then
-// sens, bp (n^2 each) and q, r (n_views * n each).
+// sens, bp (n^2 each), q, r (n_views * n each) and the back-projection's
+// per-grid partial images.
 size_t plain_candidate_bytes(const boac_geom* g) {
     size_t nn = (size_t)g->n * g->n, vb = (size_t)g->n_views * g->n_bins;
     return align256(sizeof(float) * vb * g->n) + 2 * align256(sizeof(float) * nn) +
-           2 * align256(sizeof(float) * vb);
+           2 * align256(sizeof(float) * vb) + align256(sizeof(float) * bp_partial_floats(g, 1));
+}
+
+// boac_backproject: per candidate, its table and its partial images.
+size_t backproject_candidate_bytes(const boac_geom* g) {
+    return sizeof(float) * ((size_t)g->n_views * g->n * g->n + bp_partial_floats(g, 1));
 }
 
 }  // namespace boac
@@ -69,7 +76,7 @@ extern "C" size_t boac_workspace_bytes(const boac_geom* g, int B, int op) {
     size_t vb = (size_t)g->n_views * g->n_bins;
     switch (op) {
         case BOAC_OP_PROJECT: return 0;
-        case BOAC_OP_BACKPROJECT: return align256(sizeof(float) * (size_t)B * vb * g->n);
+        case BOAC_OP_BACKPROJECT: return 2 * 256 + backproject_candidate_bytes(g) * (size_t)B;
         case BOAC_OP_MLEM: return fused_workspace_bytes(g, B);
         case BOAC_OP_MLEM_PLAIN: return plain_candidate_bytes(g);
         case BOAC_OP_SCORE: return align256(sizeof(float) * (size_t)B * vb);

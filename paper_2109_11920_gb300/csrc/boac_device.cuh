@@ -113,4 +113,30 @@ __device__ __forceinline__ float pixel_weight(float u, float w, int i, int j, in
     return r * cw;
 }
 
+// Transposed bilinear scatter of a whole sample grid, race-free without
+// atomics: G (n x n samples, row pitch WP) is added into the padded
+// accumulator img1 (row pitch P) with the weights of grid (cs, sn).  Samples
+// are split into 9 classes by (k mod 3, b mod 3); two samples of one class
+// are >= 3 lattice steps apart, i.e. more than 2 pixels apart along some
+// image axis, so their 2x2 footprints are disjoint and a class is a plain
+// read-modify-write pass.  Classes run in a fixed order (deterministic).
+// Called by all NT threads of the CTA; ends with a barrier.
+template <int N, int NT, int P, int WP>
+__device__ __forceinline__ void scatter_classes(const float* __restrict__ W, float* img1, float cs,
+                                                float sn, float c) {
+#pragma unroll
+    for (int cls = 0; cls < 9; ++cls) {
+        const int pk = cls / 3, pb = cls % 3;
+        const int nkc = (N - pk + 2) / 3, nbc = (N - pb + 2) / 3;
+        for (int t = threadIdx.x; t < nkc * nbc; t += NT) {
+            const int k = pk + 3 * (t / nbc), b = pb + 3 * (t % nbc);
+            const float g = W[k * WP + b];
+            float u, w;
+            sample_uw(k, b, cs, sn, c, &u, &w);
+            scatter_padded(img1, P, N, u, w, g);
+        }
+        __syncthreads();
+    }
+}
+
 }  // namespace boac

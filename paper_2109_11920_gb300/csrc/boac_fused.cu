@@ -135,27 +135,6 @@ __host__ __device__ constexpr size_t fused_smem_bytes(int V) {
            sizeof(double) * 32;
 }
 
-// Scatter G (W, pitch WP) into the padded accumulator img1 with the bilinear
-// weights of grid (cs, sn), class by class (see the file comment).
-template <int N, int NT>
-__device__ __forceinline__ void scatter_classes(const float* __restrict__ W, float* img1, float cs,
-                                                float sn, float c) {
-    constexpr int P = FusedShape<N, NT>::P, WP = FusedShape<N, NT>::WP;
-#pragma unroll
-    for (int cls = 0; cls < 9; ++cls) {
-        const int pk = cls / 3, pb = cls % 3;
-        const int nkc = (N - pk + 2) / 3, nbc = (N - pb + 2) / 3;
-        for (int t = threadIdx.x; t < nkc * nbc; t += NT) {
-            const int k = pk + 3 * (t / nbc), b = pb + 3 * (t % nbc);
-            const float g = W[k * WP + b];
-            float u, w;
-            sample_uw(k, b, cs, sn, c, &u, &w);
-            scatter_padded(img1, P, N, u, w, g);
-        }
-        __syncthreads();
-    }
-}
-
 // 2^x with the hardware approximation (relative error about 2^-22).
 __device__ __forceinline__ float ex2(float x) {
     float y;
@@ -337,7 +316,7 @@ __global__ void __launch_bounds__(NT, (fused_min_blocks<N, NT>())) mlem_fused_ke
                 }
             }
             __syncthreads();
-            scatter_classes<N, NT>(W, img1, cs, sn, c);
+            scatter_classes<N, NT, FusedShape<N, NT>::P, FusedShape<N, NT>::WP>(W, img1, cs, sn, c);
         }
         if (tid == 0) {  // second part of a cut candidate: wait for the first
             int ok = 1;
@@ -471,7 +450,7 @@ __global__ void __launch_bounds__(NT, (fused_min_blocks<N, NT>())) mlem_fused_ke
                     }
                 }
                 __syncthreads();
-                scatter_classes<N, NT>(W, img1, cs, sn, c);
+                scatter_classes<N, NT, FusedShape<N, NT>::P, FusedShape<N, NT>::WP>(W, img1, cs, sn, c);
             }
             if (scoring) break;
             // multiplicative update; clears the accumulator for the next pass

@@ -195,7 +195,7 @@ __global__ void grad_coef_kernel(int n, double dx, double mu_b, double mu_c, dou
 // ------------------------------------------------------------- workspace
 struct GradLayout {
     size_t mu, tab, abar, sens, sensbar, Fbar, Fnew, zbar, mubar, Fk, ck, Fseg, zseg, qseg, rseg, qK,
-        qbar, rbar, total;
+        qbar, rbar, partial, total;
 };
 
 static GradLayout grad_layout(const boac_geom* g, int B, int K, int ckpt) {
@@ -227,6 +227,7 @@ static GradLayout grad_layout(const boac_geom* g, int B, int K, int ckpt) {
     L.qK = take(Bs * vb);
     L.qbar = take(Bs * vb);
     L.rbar = take(Bs * vb);
+    L.partial = take(bp_partial_floats(g, B));
     L.total = off;
     return L;
 }
@@ -255,22 +256,20 @@ extern "C" int boac_score_grad(const boac_geom* g, const boac_tissue* t, const f
           *sensbar = P(lay.sensbar), *Fbar = P(lay.Fbar), *Fnew = P(lay.Fnew), *zbar = P(lay.zbar),
           *mubar = P(lay.mubar), *Fk = P(lay.Fk), *ck = P(lay.ck), *Fseg = P(lay.Fseg),
           *zseg = P(lay.zseg), *qseg = P(lay.qseg), *rseg = P(lay.rseg), *qK = P(lay.qK),
-          *qbar = P(lay.qbar), *rbar = P(lay.rbar);
+          *qbar = P(lay.qbar), *rbar = P(lay.rbar), *partial = P(lay.partial);
     cudaStream_t st = as_stream(stream);
     const int n = g->n, V = g->n_views;
     const float dx = g->pixel_cm;
     const size_t nn = (size_t)n * n, vb = (size_t)V * g->n_bins;
     const long long cnt_pix = (long long)B * nn, cnt_bin = (long long)B * vb;
     const dim3 rg = ray_grid(g, B);
-    const dim3 pg((unsigned)((nn + kPixThreads - 1) / kPixThreads), B);
-    const size_t smem = sizeof(float) * 2 * V;
     const int g1p = grid_1d(cnt_pix, 256), g1b = grid_1d(cnt_bin, 256);
 
     // one MLEM step F_in -> F_out, leaving q, r and z = A^T r behind
     auto mlem_step = [&](const float* F_in, float* F_o, float* q, float* r, float* z) {
         project_table_kernel<<<rg, kRayThreads, 0, st>>>(n, V, dx, tab, F_in, q);
         ratio_batched_kernel<<<g1b, 256, 0, st>>>(B, (int)vb, S, s_stride, q, r);
-        backproject_gather_kernel<<<pg, kPixThreads, smem, st>>>(n, V, dx, tab, r, z, 0);
+        backproject_table(g, B, tab, r, dx, z, 0, partial, st);
         cudaMemcpyAsync(F_o, F_in, sizeof(float) * cnt_pix, cudaMemcpyDeviceToDevice, st);
         update_kernel<<<g1p, 256, 0, st>>>((int)cnt_pix, F_o, z, sens);
     };
@@ -278,7 +277,7 @@ extern "C" int boac_score_grad(const boac_geom* g, const boac_tissue* t, const f
     int s = boac_rasterize_mu(g, t, c, B, BOAC_RASTER_AREA, mu, stream);
     if (s != BOAC_OK) return s;
     attenuation_table_kernel<<<rg, kRayThreads, 0, st>>>(n, V, dx, mu, tab);
-    backproject_gather_kernel<<<pg, kPixThreads, smem, st>>>(n, V, dx, tab, nullptr, sens, 0);
+    backproject_table(g, B, tab, nullptr, dx, sens, 0, partial, st);
     cudaMemsetAsync(abar, 0, sizeof(float) * (size_t)B * V * nn, st);
     cudaMemsetAsync(sensbar, 0, sizeof(float) * cnt_pix, st);
     // F^0 = 1 into checkpoint 0; F^{j ckpt} into checkpoint j; F^K into Fk.
@@ -307,7 +306,7 @@ extern "C" int boac_score_grad(const boac_geom* g, const boac_tissue* t, const f
     loglik_kernel<<<B, 256, 0, st>>>((int)vb, qK, S, s_stride, include_lgamma, L);
     if (F_out) cudaMemcpyAsync(F_out, Fk, sizeof(float) * cnt_pix, cudaMemcpyDeviceToDevice, st);
     qbar_final_kernel<<<g1b, 256, 0, st>>>(B, (int)vb, S, s_stride, qK, qbar);
-    backproject_gather_kernel<<<pg, kPixThreads, smem, st>>>(n, V, dx, tab, qbar, Fbar, 0);
+    backproject_table(g, B, tab, qbar, dx, Fbar, 0, partial, st);
     abar_accum_kernel<<<rg, kRayThreads, 0, st>>>(n, V, dx, qbar, Fk, nullptr, nullptr, abar);
 
     // ---- reverse through the iterations, one checkpoint segment at a time
@@ -328,7 +327,7 @@ extern "C" int boac_score_grad(const boac_geom* g, const boac_tissue* t, const f
             mlem_step_adjoint_kernel<<<g1p, 256, 0, st>>>(cnt_pix, Fbar, Fn, Fn1, z, sens, zbar, sensbar, Fnew);
             project_table_kernel<<<rg, kRayThreads, 0, st>>>(n, V, dx, tab, zbar, rbar);
             qbar_step_kernel<<<g1b, 256, 0, st>>>(B, (int)vb, S, s_stride, q, rbar, qbar);
-            backproject_gather_kernel<<<pg, kPixThreads, smem, st>>>(n, V, dx, tab, qbar, Fnew, 1);
+            backproject_table(g, B, tab, qbar, dx, Fnew, 1, partial, st);
             abar_accum_kernel<<<rg, kRayThreads, 0, st>>>(n, V, dx, r, zbar, qbar, Fn, abar);
             float* tmp = Fbar;
             Fbar = Fnew;
@@ -339,7 +338,7 @@ extern "C" int boac_score_grad(const boac_geom* g, const boac_tissue* t, const f
     abar_accum_kernel<<<rg, kRayThreads, 0, st>>>(n, V, dx, nullptr, sensbar, nullptr, nullptr, abar);
     // attenuation -> mu samples -> pixels -> coefficients
     mbar_kernel<<<rg, kRayThreads, 0, st>>>(n, V, dx, tab, abar);
-    backproject_gather_kernel<<<pg, kPixThreads, smem, st>>>(n, V, 1.0f, abar, nullptr, mubar, 0);
+    backproject_table(g, B, abar, nullptr, 1.0f, mubar, 0, partial, st);
     grad_coef_kernel<<<B, 256, 0, st>>>(n, (double)dx, (double)t->mu_b, (double)t->mu_c, (double)t->dR, c,
                                         mubar, dL_dc);
     return launch_status();

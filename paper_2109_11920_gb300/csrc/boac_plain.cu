@@ -197,21 +197,23 @@ extern "C" int boac_backproject(const boac_geom* g, const float* mu, const float
                                 float* out, void* ws, size_t ws_bytes, void* stream) {
     if (!geom_ok(g) || !mu || !out || B < 1 || B > 65535) return BOAC_EINVAL;
     const size_t nn = (size_t)g->n * g->n;
-    const size_t per = sizeof(float) * nn * g->n_views;  // one candidate's table
-    if (!ws || ws_bytes < per) return BOAC_EWORKSPACE;
-    const int chunk = (int)((ws_bytes / per) < (size_t)B ? (ws_bytes / per) : (size_t)B);
+    const size_t per = backproject_candidate_bytes(g);  // one candidate's table + partials
+    if (!ws || ws_bytes < per + 2 * 256) return BOAC_EWORKSPACE;
+    const size_t fit = (ws_bytes - 2 * 256) / per;
+    const int chunk = (int)(fit < (size_t)B ? fit : (size_t)B);
     cudaStream_t st = as_stream(stream);
-    float* tab = static_cast<float*>(ws);
-    const size_t smem = sizeof(float) * 2 * g->n_views;
+    char* base = static_cast<char*>(ws);
+    float* tab = reinterpret_cast<float*>(base);
+    float* partial = reinterpret_cast<float*>(
+        base + align256(sizeof(float) * (size_t)chunk * g->n_views * nn));
     for (int c0 = 0; c0 < B; c0 += chunk) {
         const int cb = (B - c0) < chunk ? (B - c0) : chunk;
         attenuation_table_kernel<<<ray_grid(g, cb), kRayThreads, 0, st>>>(
             g->n, g->n_views, g->pixel_cm, mu + c0 * nn, tab);
-        dim3 grid((unsigned)((nn + kPixThreads - 1) / kPixThreads), cb);
-        backproject_gather_kernel<<<grid, kPixThreads, smem, st>>>(
-            g->n, g->n_views, g->pixel_cm, tab,
-            y ? y + (size_t)c0 * g->n_views * g->n_bins : nullptr, out + c0 * nn, 0);
         int s = launch_status();
+        if (s != BOAC_OK) return s;
+        s = backproject_table(g, cb, tab, y ? y + (size_t)c0 * g->n_views * g->n_bins : nullptr,
+                              g->pixel_cm, out + c0 * nn, 0, partial, st);
         if (s != BOAC_OK) return s;
     }
     return BOAC_OK;
@@ -254,28 +256,29 @@ extern "C" int boac_mlem_plain(const boac_geom* g, const float* mu, const float*
     float* q = reinterpret_cast<float*>(base);
     base += align256(sizeof(float) * vb);
     float* r = reinterpret_cast<float*>(base);
+    base += align256(sizeof(float) * vb);
+    float* partial = reinterpret_cast<float*>(base);
     cudaStream_t st = as_stream(stream);
     const int V = g->n_views, n = g->n;
     const float dx = g->pixel_cm;
-    const size_t smem = sizeof(float) * 2 * V;
-    const dim3 pgrid((unsigned)((nn + kPixThreads - 1) / kPixThreads), 1);
     for (int cand = 0; cand < B; ++cand) {
         const float* m_c = mu + cand * nn;
         const float* S_c = S + (size_t)cand * s_stride;
         float* F_c = F + cand * nn;
         attenuation_table_kernel<<<ray_grid(g, 1), kRayThreads, 0, st>>>(n, V, dx, m_c, tab);
-        backproject_gather_kernel<<<pgrid, kPixThreads, smem, st>>>(n, V, dx, tab, nullptr, sens, 0);
+        int s = backproject_table(g, 1, tab, nullptr, dx, sens, 0, partial, st);
+        if (s != BOAC_OK) return s;
         for (int it = 0; it < K; ++it) {
             project_table_kernel<<<ray_grid(g, 1), kRayThreads, 0, st>>>(n, V, dx, tab, F_c, q);
             ratio_kernel<<<grid_1d((long long)vb, 256), 256, 0, st>>>((int)vb, S_c, q, r);
-            backproject_gather_kernel<<<pgrid, kPixThreads, smem, st>>>(n, V, dx, tab, r, bp, 0);
+            backproject_table(g, 1, tab, r, dx, bp, 0, partial, st);
             update_kernel<<<grid_1d((long long)nn, 256), 256, 0, st>>>((int)nn, F_c, bp, sens);
         }
         if (L) {
             project_table_kernel<<<ray_grid(g, 1), kRayThreads, 0, st>>>(n, V, dx, tab, F_c, q);
             loglik_kernel<<<1, 256, 0, st>>>((int)vb, q, S_c, 0, include_lgamma, L + cand);
         }
-        int s = launch_status();
+        s = launch_status();
         if (s != BOAC_OK) return s;
     }
     return BOAC_OK;

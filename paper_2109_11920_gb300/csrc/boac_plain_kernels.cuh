@@ -31,4 +31,13 @@ __global__ void loglik_kernel(int nbin, const float* __restrict__ q, const float
 dim3 ray_grid(const boac_geom* g, int B);
 int grid_1d(long long count, int threads);
 
+// out[cand] (+)= scale * sum_v B_v^T (tab_v * y_v) for B candidates from an
+// attenuation table [B][V][n][n] (boac_bpgroup.cu): grouped shared-memory
+// scatter with per-grid partial images in `partial` (bp_partial_floats(g, B)
+// floats), or the per-pixel gather where the geometry has no grouped kernel
+// (then `partial` may be null).
+size_t bp_partial_floats(const boac_geom* g, int B);
+int backproject_table(const boac_geom* g, int B, const float* tab, const float* y, float scale, float* out,
+                      int accumulate, float* partial, cudaStream_t st);
+
 }  // namespace boac

@@ -68,4 +68,5 @@ def test_host_side_argument_checks(lib):
     assert lib.boac_score(ctypes.byref(good), fake, fake, 0, fake, 1, 1, fake, None, 0, None) == _lib.BOAC_EWORKSPACE
     assert lib.boac_backproject(ctypes.byref(good), fake, None, 1, fake, None, 0, None) == _lib.BOAC_EWORKSPACE
     assert lib.boac_workspace_bytes(ctypes.byref(good), 1, _lib.OP_PROJECT) == 0
-    assert lib.boac_workspace_bytes(ctypes.byref(good), 3, _lib.OP_BACKPROJECT) == 3 * 60 * 64 * 64 * 4
+    # per candidate: its attenuation table (60 views) and 15 per-grid partial images
+    assert lib.boac_workspace_bytes(ctypes.byref(good), 3, _lib.OP_BACKPROJECT) == 512 + 3 * (60 + 15) * 64 * 64 * 4

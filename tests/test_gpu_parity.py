@@ -208,3 +208,24 @@ def test_work_split_status_and_odd_batches(cuda, probs):
         assert boac.boac_workspace_status(ws) == boac._lib.BOAC_OK
         torch.testing.assert_close(F, F1.expand(B, p.n, p.n), rtol=0, atol=0)
         torch.testing.assert_close(L, L1.expand(B), rtol=0, atol=0)
+
+
+def test_mlem_invariants_on_gpu(cuda, probs):
+    """EM properties of the CUDA path itself (any size): counts preserved,
+    sum(A F^{k+1}) = sum(S) over rays with q > 0; images non-negative; the
+    likelihood never decreases from one iteration to the next."""
+    p = probs[SHAPES[2]]
+    g = geom(p)
+    mu = T(p.mu, cuda)
+    S = T(p.S, cuda)
+    prev = None
+    for K in range(1, 7):
+        F = torch.ones(3, p.n, p.n, device=cuda)
+        F, L = boac.boac_mlem(g, mu, S, F, K, include_lgamma=False)
+        assert float(F.min()) >= 0.0
+        q = boac.boac_project(g, mu, F).double()
+        for b in range(3):
+            np.testing.assert_allclose(float(q[b].sum()), float(S.double().sum()), rtol=2e-5)
+        if prev is not None:
+            assert torch.all(L >= prev - 1e-7 * prev.abs())
+        prev = L
