@@ -541,7 +541,8 @@ def run_workload(args):
                     f"K ~ U{{20..80}}, own phantom per candidate")
         else:
             wl = synth.LARGE
-            n_sl, per = wl.extra["slices"], wl.B
+            n_sl, per = args.slices or wl.extra["slices"], wl.B
+            K_l = args.wl_iters or wl.K
             c_sl = synth.slice_coefficients(np.random.default_rng(wl.seed), n_sl)
             g, t, S_list = _phantom_sinograms(boac, Geom, Tissue, dev, wl.n, wl.dx, wl.V, wl.counts,
                                               list(range(n_sl)), c_true=c_sl)
@@ -551,9 +552,9 @@ def run_workload(args):
                 mu_c = boac.boac_rasterize_mu(g, t, cc)
                 mus += list(mu_c)
                 Ss += [S_list[s]] * per
-            batch = boac.RaggedBatch([g], [0] * (n_sl * per), [wl.K] * (n_sl * per), mus, Ss, device=dev)
-            work = [(wl.V, wl.n, wl.K)] * (n_sl * per)
-            desc = f"{wl.name}: {n_sl} slices x {per} candidates, 256x256, 180 views, K={wl.K}"
+            batch = boac.RaggedBatch([g], [0] * (n_sl * per), [K_l] * (n_sl * per), mus, Ss, device=dev)
+            work = [(wl.V, wl.n, K_l)] * (n_sl * per)
+            desc = f"{wl.name}: {n_sl} slices x {per} candidates, 256x256, 180 views, K={K_l}"
         config = autotune.tune_ragged(batch, probe_iters=2, repeats=1) if not args.no_tune else None
         batch.prepare(config)
         ms = _timed(lambda: (batch.F_pool.fill_(1.0), batch.run()), dev, reps=1 if name == "large" else 2)
@@ -596,6 +597,8 @@ def main():
     ap.add_argument("--iters", type=int, default=WL.K, help="MLEM iterations")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-path comparison")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffer) timing")
+    ap.add_argument("--slices", type=int, default=0, help="large workload: slices (default 64)")
+    ap.add_argument("--wl-iters", type=int, default=0, help="large workload: MLEM iterations (default 100)")
     ap.add_argument("--workload", default="batched", choices=["batched", "small", "ragged", "large", "grad"],
                     help="batched: the benchmark; the others print their own throughput line")
     ap.add_argument("--no-tune", action="store_true", help="ragged/large: default launch shapes")

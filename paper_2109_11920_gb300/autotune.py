@@ -62,7 +62,8 @@ def tune_ragged(batch: "api.RaggedBatch", probe_iters: int = 3, repeats: int = 2
             Ss.append(batch.S_pool[d.S_off:d.S_off + g.n_views * g.n_bins].view(g.n_views, g.n_bins))
         sub = api.RaggedBatch([g], [0] * len(members), [probe_iters] * len(members), mus, Ss,
                               device=batch.device)
-        times = {cfg: _time_config(sub, cfg, repeats) for cfg in range(api.N_CONFIGS)}
+        times = {cfg: _time_config(sub, cfg, repeats) for cfg in range(api.N_CONFIGS)
+                 if api.config_valid(g, cfg)}
         best = min(times, key=times.get)
         if times[best] == float("inf"):
             raise RuntimeError(f"no launch configuration runs for class {g}")

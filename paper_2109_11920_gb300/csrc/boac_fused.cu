@@ -33,56 +33,10 @@
 #include <vector>
 
 #include "boac_device.cuh"
+#include "boac_fused.h"
 #include "boac_internal.h"
 
 namespace boac {
-
-struct RaggedDesc {
-    long long mu_off, S_off, F_off;  // float offsets into the caller's pools
-    int K;                           // MLEM iterations of this candidate
-    int out;                         // index of its score in L
-};
-
-struct FusedArgs {
-    const float* mu;
-    const float* S;
-    long long s_stride;
-    float* F;
-    double* L;
-    int include_lgamma;
-    int B, V, K;
-    float dx;
-    // Per-CTA slots, written and read by the same CTA within one launch:
-    // read with plain (coherent) loads, never through the read-only path.
-    float* tab;   // [slots][tab_floats]: attenuation exponents, see below
-    float* sens;  // [slots][n][n]
-    // Images above 128 x 128 do not fit shared memory: their F, accumulator
-    // and sample buffer live in a per-slot region of the workspace instead
-    // (same layout), read through L1 and written through to L2.
-    float* img;   // [slots][2 IMG + n WP] or unused
-    // Ragged batches: per-candidate records (device), sorted by the host;
-    // nullptr: uniform batch, candidate b at b * n^2 / b * s_stride, K = K.
-    const RaggedDesc* desc;
-    // Work split.  The batch's iterations are laid end to end, candidate
-    // after candidate (candidate j occupies units [job_start[j],
-    // job_start[j+1]), max(K, 1) units each; job_start == nullptr for a
-    // uniform batch), and CTA m runs units [m cap, (m+1) cap) with
-    // cap >= the longest candidate (McNaughton's wrap-around rule: every CTA
-    // gets the same share, a candidate is cut between at most two CTAs).
-    // A CTA takes its candidates in descending order, so the first part of
-    // a cut candidate runs first on CTA m and its second part last on CTA
-    // m+1; ready[j] tells the second part that the first has written F
-    // (always long before it is needed, since cap >= the candidate length).
-    const long long* job_start;
-    long long cap;
-    int* ready;    // [B] zeroed before the launch
-    int* status;   // 0, or BOAC_ETIMEOUT if a bounded wait ran out
-};
-
-// Cycles a CTA waits for the first part of a cut candidate before giving up
-// (about 8 s at 2 GHz; the schedule leaves it a whole candidate's worth of
-// slack, so the wait ends immediately in practice).
-constexpr long long kReadySpinCycles = 1LL << 34;
 
 // Shared-memory and work layout of one CTA (image side N, NT threads).
 template <int N, int NT>
@@ -133,26 +87,6 @@ __host__ __device__ constexpr size_t fused_smem_bytes(int V) {
     return sizeof(float) * ((fused_global_images(N) ? 0 : fused_image_floats<N, NT>()) +
                             4 * L::NSEG * N + 4 * N + 2 * ((V + 1) / 2) * 2) +
            sizeof(double) * 32;
-}
-
-// 2^x with the hardware approximation (relative error about 2^-22).
-__device__ __forceinline__ float ex2(float x) {
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-// Ask L2 to fetch the 128-byte line holding p (no register result).
-__device__ __forceinline__ void prefetch_l2(const void* p) {
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-}
-
-__device__ __forceinline__ double loglik_term(double s, double q, int include_lgamma) {
-    double t;
-    if (s > 0.0) t = q > 0.0 ? s * log(q) - q : -INFINITY;
-    else t = -q;
-    if (include_lgamma) t -= lgamma(s + 1.0);
-    return t;
 }
 
 // CTAs per SM the register allocation is sized for: as many as shared memory
@@ -489,17 +423,22 @@ __global__ void __launch_bounds__(NT, (fused_min_blocks<N, NT>())) mlem_fused_ke
 
 // ---------------------------------------------------------------- host side
 // Launch shapes: for each image side, CTAs of 2n, 4n or 8n threads (at most
-// 1024), with four or two views per sample grid.  Configuration id =
-// 2 * shape + (1 for two views per grid).
+// 1024), with four or two views per sample grid: configuration id =
+// 2 * shape + (1 for two views per grid).  For 256 x 256 images, ids 6, 7
+// and 8 are the cluster kernel (boac_band.cu) with 5, 6 or 8 CTAs per
+// candidate (four views per grid only).
 constexpr int kShapes = 3;
-constexpr int kConfigs = 2 * kShapes;
+constexpr int kBandConfigs = 3;
+constexpr int kConfigs = 2 * kShapes + kBandConfigs;
 
 struct FusedVariant {
     int n, nt;
     bool quad;
+    int nb;  // CTAs per candidate: 1, or the cluster size of the band kernel
     size_t (*smem)(int V);
     const void* func;
-    int (*launch)(const FusedArgs& a, int slots, cudaStream_t st);
+    // `holders`: CTAs (nb == 1) or clusters that share the work
+    int (*launch)(const FusedArgs& a, int holders, cudaStream_t st);
 };
 
 template <int N, int NT, bool QUAD>
@@ -524,21 +463,34 @@ static size_t smem_of(int V) { return fused_smem_bytes<N, NT>(V); }
 
 template <int N, int NT, bool QUAD>
 static FusedVariant make_variant() {
-    return FusedVariant{N, NT, QUAD, smem_of<N, NT>, (const void*)mlem_fused_kernel<N, NT, QUAD>,
+    return FusedVariant{N, NT, QUAD, 1, smem_of<N, NT>, (const void*)mlem_fused_kernel<N, NT, QUAD>,
                         fused_launch_t<N, NT, QUAD>};
 }
 
+template <int NB>
+static size_t band_smem_of(int) { return band_smem_bytes(NB); }
+template <int NB>
+static int band_launch_of(const FusedArgs& a, int clusters, cudaStream_t st) {
+    return band_launch(NB, a, clusters, st);
+}
+template <int NB>
+static FusedVariant make_band_variant() {
+    return FusedVariant{256, 1024, true, NB, band_smem_of<NB>, nullptr, band_launch_of<NB>};
+}
+
 #define BOAC_SHAPES(NV)                                                                        \
-    {make_variant<NV, 2 * NV, true>(), make_variant<NV, 2 * NV, false>(),                      \
-     make_variant<NV, 4 * NV, true>(), make_variant<NV, 4 * NV, false>(),                      \
-     make_variant<NV, (8 * NV > 1024 ? 1024 : 8 * NV), true>(),                                \
-     make_variant<NV, (8 * NV > 1024 ? 1024 : 8 * NV), false>()}
+    make_variant<NV, 2 * NV, true>(), make_variant<NV, 2 * NV, false>(),                       \
+        make_variant<NV, 4 * NV, true>(), make_variant<NV, 4 * NV, false>(),                   \
+        make_variant<NV, (8 * NV > 1024 ? 1024 : 8 * NV), true>(),                             \
+        make_variant<NV, (8 * NV > 1024 ? 1024 : 8 * NV), false>()
+#define BOAC_NO_BAND FusedVariant{}, FusedVariant{}, FusedVariant{}
 
 static const FusedVariant* variant_table(int n) {
-    static const FusedVariant t64[kConfigs] = BOAC_SHAPES(64);
-    static const FusedVariant t96[kConfigs] = BOAC_SHAPES(96);
-    static const FusedVariant t128[kConfigs] = BOAC_SHAPES(128);
-    static const FusedVariant t256[kConfigs] = BOAC_SHAPES(256);
+    static const FusedVariant t64[kConfigs] = {BOAC_SHAPES(64), BOAC_NO_BAND};
+    static const FusedVariant t96[kConfigs] = {BOAC_SHAPES(96), BOAC_NO_BAND};
+    static const FusedVariant t128[kConfigs] = {BOAC_SHAPES(128), BOAC_NO_BAND};
+    static const FusedVariant t256[kConfigs] = {BOAC_SHAPES(256), make_band_variant<5>(),
+                                                make_band_variant<6>(), make_band_variant<8>()};
     switch (n) {
         case 64: return t64;
         case 96: return t96;
@@ -548,19 +500,41 @@ static const FusedVariant* variant_table(int n) {
     }
 }
 
-// Default configuration: the largest CTA that keeps >= 64 registers per
-// thread at the occupancy shared memory allows; four views per grid when
-// V % 4 == 0.
-static int default_config(const boac_geom* g) {
+// Default configuration of the one-CTA kernel: the largest CTA that keeps
+// >= 64 registers per thread at the occupancy shared memory allows; four
+// views per grid when V % 4 == 0.
+static int single_cta_config(const boac_geom* g) {
     const int shape = g->n == 64 ? 1 : 2;
     return 2 * shape + (g->n_views % 4 == 0 ? 0 : 1);
+}
+
+// Default configuration: 256 x 256 images with V % 4 == 0 take the cluster
+// kernel with the cluster size that keeps the most SMs busy (clusters are
+// placed within one GPC, so the resident count depends on the size); the
+// smaller cluster on a tie.
+static int default_config(const boac_geom* g) {
+    if (g->n == 256 && g->n_views % 4 == 0) {
+        static const int nbs[kBandConfigs] = {5, 6, 8};
+        int best = -1, best_ctas = 0;
+        for (int i = 0; i < kBandConfigs; ++i) {
+            const int ctas = band_max_clusters(nbs[i]) * nbs[i];
+            if (ctas > best_ctas) {
+                best = i;
+                best_ctas = ctas;
+            }
+        }
+        if (best >= 0) return 2 * kShapes + best;
+    }
+    return single_cta_config(g);
 }
 
 static const FusedVariant* get_variant(const boac_geom* g, int config) {
     const FusedVariant* t = variant_table(g->n);
     if (!t || config < 0 || config >= kConfigs) return nullptr;
     const FusedVariant* v = &t[config];
+    if (!v->launch) return nullptr;
     if (v->quad ? (g->n_views % 4 != 0) : (g->n_views % 2 != 0)) return nullptr;
+    if (v->nb > 1 && !band_supported(g->n, g->n_views, v->nb)) return nullptr;
     return v;
 }
 
@@ -594,47 +568,66 @@ static int variant_occupancy(const FusedVariant* v, int V) {
     return nb;
 }
 
-// Workspace of the fused kernel for `slots` CTA slots and B candidates:
+// Workspace of the fused kernels for `holders` CTAs (or clusters) and B
+// candidates:
 //   [0, 256)   status word (BOAC_OK, or BOAC_ETIMEOUT from a bounded wait)
-//   tables     attenuation exponents, one region per slot
-//   sens       sensitivity image per slot
-//   images     padded F / accumulator / sample buffer per slot (n > 128)
+//   tables     attenuation exponents, one region per CTA
+//   sens       sensitivity image (cluster kernel: band rows) per CTA
+//   images     one-CTA kernel, n > 128: padded F / accumulator / sample
+//              buffer per CTA; cluster kernel: the record kernel's flag and
+//              the ray-run records of every (band, grid)
 //   ready      one flag per candidate (the work split's hand-over)
 struct FusedLayout {
-    size_t status, tab, sens, img, ready, total;
+    size_t status, tab, sens, img, geo, ready, total;
 };
 
-static FusedLayout fused_layout(const boac_geom* g, int slots, int B) {
+static FusedLayout fused_layout(const boac_geom* g, const FusedVariant* v, int holders, int B) {
     FusedLayout l;
+    const size_t ctas = (size_t)holders * v->nb;
     l.status = 0;
     l.tab = 256;
-    l.sens = l.tab + align256(sizeof(float) * (size_t)slots * fused_tab_floats(g->n, g->n_views));
-    l.img = l.sens + align256(sizeof(float) * (size_t)slots * g->n * g->n);
-    // padded F and accumulator, (n+1)(n+2)+1 floats each, and the n x (n+1)
-    // sample buffer, for sides held in global memory
-    const size_t img_floats = fused_global_images(g->n)
-                                  ? 2 * ((size_t)(g->n + 1) * (g->n + 2) + 1) + (size_t)g->n * (g->n + 1)
-                                  : 0;
-    l.ready = l.img + align256(sizeof(float) * (size_t)slots * img_floats);
+    if (v->nb > 1) {
+        l.sens = l.tab + align256(sizeof(float) * ctas * band_tab_floats(v->nb, g->n_views));
+        l.img = l.sens + align256(sizeof(float) * ctas * band_sens_floats(v->nb));
+        l.geo = l.img + 256;
+        l.ready = l.geo + align256(band_geo_bytes(v->nb, g->n_views));
+    } else {
+        l.sens = l.tab + align256(sizeof(float) * ctas * fused_tab_floats(g->n, g->n_views));
+        l.img = l.sens + align256(sizeof(float) * ctas * g->n * g->n);
+        // padded F and accumulator, (n+1)(n+2)+1 floats each, and the
+        // n x (n+1) sample buffer, for sides held in global memory
+        const size_t img_floats = fused_global_images(g->n)
+                                      ? 2 * ((size_t)(g->n + 1) * (g->n + 2) + 1) + (size_t)g->n * (g->n + 1)
+                                      : 0;
+        l.geo = l.img + align256(sizeof(float) * ctas * img_floats);
+        l.ready = l.geo;
+    }
     l.total = l.ready + align256(sizeof(int) * (size_t)B);
     return l;
 }
 
-static int variant_slots(const boac_geom* g, const FusedVariant* v, int B) {
-    const int per_sm = variant_occupancy(v, g->n_views);
-    if (per_sm <= 0) return 0;
-    const long long slots = (long long)per_sm * sm_count();
-    return (int)(slots < B ? slots : B);
+// CTAs (one-CTA kernel) or clusters that run at once, at most B.
+static int variant_holders(const boac_geom* g, const FusedVariant* v, int B) {
+    long long h;
+    if (v->nb > 1) {
+        h = band_max_clusters(v->nb);
+    } else {
+        const int per_sm = variant_occupancy(v, g->n_views);
+        h = (long long)per_sm * sm_count();
+    }
+    if (h <= 0) return 0;
+    return (int)(h < B ? h : B);
 }
 
 int fused_slots(const boac_geom* g, int B) {
     const FusedVariant* v = get_variant(g, default_config(g));
-    return v ? variant_slots(g, v, B) : 0;
+    return v ? variant_holders(g, v, B) : 0;
 }
 
 size_t fused_workspace_bytes(const boac_geom* g, int B) {
-    const int slots = fused_slots(g, B);
-    return slots > 0 ? fused_layout(g, slots, B).total : 0;
+    const FusedVariant* v = get_variant(g, default_config(g));
+    const int h = v ? variant_holders(g, v, B) : 0;
+    return h > 0 ? fused_layout(g, v, h, B).total : 0;
 }
 
 // Units per CTA of the work split: the larger of an even share and the
@@ -666,6 +659,8 @@ static FusedArgs base_args(const boac_geom* g, const float* mu, const float* S, 
     a.cap = 0;
     a.ready = reinterpret_cast<int*>(ws + l.ready);
     a.status = reinterpret_cast<int*>(ws + l.status);
+    a.geo = reinterpret_cast<const int*>(ws + l.geo);
+    a.geo_bad = reinterpret_cast<int*>(ws + l.img);
     return a;
 }
 
@@ -674,7 +669,7 @@ static FusedArgs base_args(const boac_geom* g, const float* mu, const float* S, 
 static int launch_uniform(const boac_geom* g, const FusedVariant* v, int slots, const float* mu,
                           const float* S, long long s_stride, float* F, int K, int B, double* L,
                           int include_lgamma, char* ws, cudaStream_t st) {
-    const FusedLayout l = fused_layout(g, slots, B);
+    const FusedLayout l = fused_layout(g, v, slots, B);
     FusedArgs a = base_args(g, mu, S, s_stride, F, K, B, L, include_lgamma, ws, l);
     const long long per = K > 0 ? K : 1, units = (long long)B * per;
     a.cap = split_cap(units, per, slots);
@@ -717,14 +712,14 @@ static int ragged_plan(const boac_geom* classes, int n_classes, const boac_ragge
         pl->var[c] = get_variant(&classes[c], cfg);
         if (!pl->var[c]) return BOAC_EINVAL;
         const int cnt = pl->cls_count[c];
-        pl->slots[c] = cnt ? variant_slots(&classes[c], pl->var[c], cnt) : 0;
+        pl->slots[c] = cnt ? variant_holders(&classes[c], pl->var[c], cnt) : 0;
         if (cnt && pl->slots[c] <= 0) return BOAC_ECUDA;
         pl->desc_off[c] = off;
         off += align256(sizeof(RaggedDesc) * (size_t)cnt);
         pl->start_off[c] = off;
         off += align256(sizeof(long long) * ((size_t)cnt + 1));
         pl->layout_off[c] = off;
-        off += cnt ? fused_layout(&classes[c], pl->slots[c], cnt).total : 0;
+        off += cnt ? fused_layout(&classes[c], pl->var[c], pl->slots[c], cnt).total : 0;
     }
     pl->total = off;
     return BOAC_OK;
@@ -753,9 +748,9 @@ extern "C" int boac_mlem(const boac_geom* g, const float* mu, const float* S, lo
     if (g->n_views % 2) return BOAC_EINVAL;
     const FusedVariant* v = get_variant(g, default_config(g));
     if (!v) return BOAC_EUNSUPPORTED;
-    const int slots = variant_slots(g, v, B);
+    const int slots = variant_holders(g, v, B);
     if (slots <= 0) return BOAC_ECUDA;
-    if (!ws || ws_bytes < fused_layout(g, slots, B).total) return BOAC_EWORKSPACE;
+    if (!ws || ws_bytes < fused_layout(g, v, slots, B).total) return BOAC_EWORKSPACE;
     return launch_uniform(g, v, slots, mu, S, s_stride, F, K, B, L, include_lgamma,
                           static_cast<char*>(ws), as_stream(stream));
 }
@@ -829,7 +824,7 @@ extern "C" int boac_mlem_ragged_run(const boac_geom* classes, int n_classes,
     for (int c = 0; c < n_classes; ++c) {
         const int cnt = pl.cls_count[c];
         if (cnt == 0) continue;
-        const FusedLayout l = fused_layout(&classes[c], pl.slots[c], cnt);
+        const FusedLayout l = fused_layout(&classes[c], pl.var[c], pl.slots[c], cnt);
         char* cbase = base + pl.layout_off[c];
         FusedArgs a = base_args(&classes[c], mu_pool, S_pool, 0, F_pool, 0, cnt, L, include_lgamma, cbase, l);
         a.desc = reinterpret_cast<const RaggedDesc*>(base + pl.desc_off[c]);
@@ -899,9 +894,9 @@ static void* noalloc_scratch_ptr() {
 // Largest number of resident CTA slots whose tables, sensitivity images and
 // the candidates' hand-over flags fit the built-in scratch (0 if not even
 // one slot does).
-static int noalloc_slots(const boac_geom* g, int B) {
-    int slots = fused_slots(g, B);
-    while (slots > 0 && fused_layout(g, slots, B).total > kNoAllocScratchBytes) --slots;
+static int noalloc_slots(const boac_geom* g, const FusedVariant* v, int B) {
+    int slots = variant_holders(g, v, B);
+    while (slots > 0 && fused_layout(g, v, slots, B).total > kNoAllocScratchBytes) --slots;
     return slots;
 }
 
@@ -912,10 +907,11 @@ extern "C" int boac_mlem_noalloc(const boac_geom* g, const float* mu, const floa
                                  int include_lgamma, void* stream) {
     if (!geom_ok(g) || !mu || !S || !F || B < 1 || K < 0 || s_stride < 0) return BOAC_EINVAL;
     if (g->n_views % 2) return BOAC_EINVAL;
-    const FusedVariant* v = get_variant(g, default_config(g));
+    // the one-CTA kernel: its per-CTA scratch is the smallest
+    const FusedVariant* v = get_variant(g, single_cta_config(g));
     if (!v) return BOAC_EUNSUPPORTED;
-    if (fused_slots(g, B) <= 0) return BOAC_ECUDA;
-    const int slots = noalloc_slots(g, B);
+    if (variant_holders(g, v, B) <= 0) return BOAC_ECUDA;
+    const int slots = noalloc_slots(g, v, B);
     if (slots <= 0) return BOAC_EWORKSPACE;  // one candidate's scratch exceeds 64 MiB
     void* scratch = noalloc_scratch_ptr();
     if (!scratch) return BOAC_ECUDA;

@@ -1,0 +1,98 @@
+// boac_fused.h -- declarations shared by the two fused MLEM kernels: the
+// one-CTA-per-candidate kernel (boac_fused.cu, images up to 128 x 128 held
+// in one SM's shared memory) and the cluster kernel (boac_band.cu, 256 x 256
+// images split into bands of rows over the CTAs of a thread-block cluster).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "boac_internal.h"
+
+namespace boac {
+
+struct RaggedDesc {
+    long long mu_off, S_off, F_off;  // float offsets into the caller's pools
+    int K;                           // MLEM iterations of this candidate
+    int out;                         // index of its score in L
+};
+
+struct FusedArgs {
+    const float* mu;
+    const float* S;
+    long long s_stride;
+    float* F;
+    double* L;
+    int include_lgamma;
+    int B, V, K;
+    float dx;
+    // Per-CTA slots, written and read by the same CTA within one launch:
+    // read with plain (coherent) loads, never through the read-only path.
+    float* tab;   // [slots][tab_floats]: attenuation exponents
+    float* sens;  // [slots][n][n] (cluster kernel: [CTAs][band rows][n])
+    // Images above 128 x 128 do not fit shared memory: their F, accumulator
+    // and sample buffer live in a per-slot region of the workspace instead
+    // (same layout), read through L1 and written through to L2.
+    float* img;   // [slots][2 IMG + n WP] or unused
+    // Ragged batches: per-candidate records (device), sorted by the host;
+    // nullptr: uniform batch, candidate b at b * n^2 / b * s_stride, K = K.
+    const RaggedDesc* desc;
+    // Work split.  The batch's iterations are laid end to end, candidate
+    // after candidate (candidate j occupies units [job_start[j],
+    // job_start[j+1]), max(K, 1) units each; job_start == nullptr for a
+    // uniform batch), and CTA (or cluster) m runs units [m cap, (m+1) cap) with
+    // cap >= the longest candidate (McNaughton's wrap-around rule: every CTA
+    // gets the same share, a candidate is cut between at most two CTAs).
+    // A CTA takes its candidates in descending order, so the first part of
+    // a cut candidate runs first on CTA m and its second part last on CTA
+    // m+1; ready[j] tells the second part that the first has written F
+    // (always long before it is needed, since cap >= the candidate length).
+    const long long* job_start;
+    long long cap;
+    int* ready;    // [B] zeroed before the launch
+    int* status;   // 0, or BOAC_ETIMEOUT if a bounded wait ran out
+    // Cluster kernel only: the ray-run records of every (band, grid), and a
+    // flag the record kernel sets if a run exceeds the kernel's buffers.
+    const int* geo;
+    int* geo_bad;
+};
+
+// Cycles a CTA waits for the first part of a cut candidate before giving up
+// (about 8 s at 2 GHz; the schedule leaves it a whole candidate's worth of
+// slack, so the wait ends immediately in practice).
+constexpr long long kReadySpinCycles = 1LL << 34;
+
+// 2^x with the hardware approximation (relative error about 2^-22).
+__device__ __forceinline__ float ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Ask L2 to fetch the 128-byte line holding p (no register result).
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+__device__ __forceinline__ double loglik_term(double s, double q, int include_lgamma) {
+    double t;
+    if (s > 0.0) t = q > 0.0 ? s * log(q) - q : -INFINITY;
+    else t = -q;
+    if (include_lgamma) t -= lgamma(s + 1.0);
+    return t;
+}
+
+// ---- cluster kernel (boac_band.cu): images of side 256, V % 4 == 0, a
+// cluster of nb CTAs per candidate, nb in {5, 6, 8}.
+bool band_supported(int n, int V, int nb);
+size_t band_smem_bytes(int nb);
+size_t band_tab_floats(int nb, int V);   // attenuation exponents, per CTA
+size_t band_sens_floats(int nb);         // sensitivity rows, per CTA
+size_t band_geo_bytes(int nb, int V);    // per-band ray-run records
+// Largest number of clusters of nb CTAs resident at once (cached per device;
+// 0 if the device cannot run them).
+int band_max_clusters(int nb);
+// Launch the record kernel and the cluster kernel with `clusters` clusters.
+int band_launch(int nb, const FusedArgs& a, int clusters, cudaStream_t st);
+
+}  // namespace boac

@@ -51,8 +51,9 @@ def test_every_launch_configuration_agrees(cuda):
     batch, _ = build(cuda, cls, K, seed0=200)
     L0 = boac.boac_mlem_ragged(batch).clone()
     F0 = batch.F_pool.clone()
-    for cfg in range(boac.N_CONFIGS):
+    for cfg in range(boac.N_SINGLE_CTA_CONFIGS):
         config = [cfg if (cfg % 2 == 1 or g.n_views % 4 == 0) else cfg + 1 for g in batch.classes]
+        assert all(boac.config_valid(g, c) for g, c in zip(batch.classes, config))
         batch.F_pool.fill_(1.0)
         L = boac.boac_mlem_ragged(batch, config=config)
         assert rel_l2(batch.F_pool.cpu().numpy(), F0.cpu().numpy()) < 1e-5, config
