@@ -49,12 +49,36 @@ namespace cg = cooperative_groups;
 
 namespace boac {
 
+// First image row of band r (r = NB: n).  Equal bands leave the CTAs of the
+// middle bands waiting less than the outer ones: near 45 degrees the
+// rotated sample grid misses the image's corners, so the outer bands hold
+// fewer samples.  For 5 bands the heights 52, 51, 49, 51, 53 lower the sum
+// over the 180-view grids of the busiest band's samples by 5 % (sizes found
+// by a local search of that sum); the other cluster sizes gain nothing
+// within their shared-memory room and use equal heights.
+template <int NB>
+__host__ __device__ constexpr int band_start(int r) {
+    if (NB == 5)
+        return r <= 0 ? 0 : r == 1 ? 52 : r == 2 ? 103 : r == 3 ? 152 : r == 4 ? 203 : 256;
+    return r * ((256 + NB - 1) / NB) < 256 ? r * ((256 + NB - 1) / NB) : 256;
+}
+
+template <int NB>
+__host__ __device__ constexpr int band_max_rows() {
+    int h = 0;
+    for (int r = 0; r < NB; ++r) h = band_start<NB>(r + 1) - band_start<NB>(r) > h ? band_start<NB>(r + 1) - band_start<NB>(r) : h;
+    return h;
+}
+
 template <int NB>
 struct BandShape {
     static constexpr int N = 256;
     static constexpr int NT = 1024;
-    static constexpr int H = (N + NB - 1) / NB;   // rows per band (the last band: the rest)
-    static constexpr int P = N + 1;               // padded row pitch
+    static constexpr int H = band_max_rows<NB>();  // rows of the tallest band
+    // Padded band image: pixel (i, j), j in [-1, n], at local row i - R0 + 1,
+    // column j + 1; the right padding column of a row and the left padding
+    // column of the next are the same zero cell.
+    static constexpr int P = N + 1;
     static constexpr int BIMG = (H + 2) * P + 1;  // band + the rows above and below
     static constexpr int WP = N + 1;              // sample-buffer pitch
     // Longest in-band run of a column: the band's H (+1 for the row above
@@ -64,16 +88,18 @@ struct BandShape {
     static constexpr int SC = (LC + TC - 1) / TC; // column-run steps per thread
     static constexpr int SR = (LC + 1) / 2;       // row-run steps per thread (bound)
     static constexpr int REC = 8 + 4 * N;         // ints per (band, grid) record
-    static constexpr size_t GSTRIDE = (size_t)(SC + SR) * NT + 2 * N;  // table floats per grid
-    static_assert((NB - 1) * H < N, "every band owns at least one row");
+    // table floats per grid: Xc (column-run order), XrT (row-run order), Uc, Ur
+    static constexpr size_t GSTRIDE = (size_t)(SC + SR) * NT + 2 * N;
+    static_assert(band_start<NB>(NB - 1) < N && band_start<NB>(NB) == N, "every band owns a row");
     static_assert(TC * N == NT && 4 * N == NT, "thread mapping");
 };
 
 // Record layout per (band, grid): [0] first active row kmin, [1] active rows
-// R, [2] threads per row T, [3] column steps, [4] row steps, [5..7] unused,
+// R, [2] threads per row T, [3] column steps, [4] row steps, [5], [6] the
+// base view's cos and sin (float bits), [7] unused,
 // then col_lo[n], col_len[n] (the run of column b: k in [lo, lo + len)),
 // row_lo[n], row_len[n] (the run of row k: b in [lo, lo + len)).
-enum { kRecKmin = 0, kRecRows = 1, kRecT = 2, kRecSc = 3, kRecSr = 4, kRecHdr = 8 };
+enum { kRecKmin = 0, kRecRows = 1, kRecT = 2, kRecSc = 3, kRecSr = 4, kRecCos = 5, kRecSin = 6, kRecHdr = 8 };
 
 // Base view of grid gi (views gi + j V/4): gi itself when its angle is at
 // most 45 degrees, else gi - V/4 (= gi + 3V/4), whose angle is in (-45, 0).
@@ -82,13 +108,16 @@ __host__ __device__ __forceinline__ int band_base_view(int gi, int V) {
 }
 
 // Band of a sample whose footprint's top row is fi (fi = -1: band 0).
-template <int H>
+template <int NB>
 __device__ __forceinline__ int band_of_row(int fi) {
-    return fi < 0 ? 0 : fi / H;
+    int r = 0;
+#pragma unroll
+    for (int q = 1; q < NB; ++q) r += fi >= band_start<NB>(q);
+    return r;
 }
 
-// Bilinear sample / transposed scatter in a band image whose local row 0 is
-// image row R0 - 1; the sample is known to lie in the band.
+// Bilinear sample / transposed scatter in a padded band image whose local
+// row 0 is image row R0 - 1; the sample is known to lie in the band.
 template <int P>
 __device__ __forceinline__ float bilerp_band(const float* img, int R0, float u, float w) {
     const float fj = floorf(u), fi = floorf(w);
@@ -141,7 +170,7 @@ __global__ void __launch_bounds__(256) band_records_kernel(int V, int* geo, int*
     for (int k = 0; k < N; ++k) {
         float u, w;
         sample_uw(k, t, cs, sn, c, &u, &w);
-        if (inside_open(u, w, N) && band_of_row<S::H>((int)floorf(w)) == r) {
+        if (inside_open(u, w, N) && band_of_row<NB>((int)floorf(w)) == r) {
             if (lo < 0) lo = k;
             hi = k;
             ++cnt;
@@ -185,13 +214,16 @@ __global__ void __launch_bounds__(256) band_records_kernel(int V, int* geo, int*
         rec[kRecT] = T;
         rec[kRecSc] = s_sc;
         rec[kRecSr] = s_sr;
+        rec[kRecCos] = __float_as_int(cs);
+        rec[kRecSin] = __float_as_int(sn);
         if (s_bad || s_sc > S::SC || s_sr > S::SR) atomicExch(bad, 1);
     }
 }
 
 // ---------------------------------------------------------------- kernel
-// Shared-memory layout (bytes): 32 doubles for the score reduction, 4 ints of
-// flags, then floats.
+// Shared-memory layout (bytes): 32 doubles for the score reduction, 16 ints
+// of flags, then floats, then two slots holding a grid's record (copied
+// from global memory with cp.async).
 template <int NB>
 struct BandSmem {
     using S = BandShape<NB>;
@@ -201,12 +233,13 @@ struct BandSmem {
     static constexpr int PUB0 = W0 + S::LC * S::WP;     // [2][4][n] published partial sums
     static constexpr int CP0 = PUB0 + 8 * S::N;         // [2][TC][n] column-run partials
     static constexpr int RP0 = CP0 + 2 * S::TC * S::N;  // [2][NT] row-run partials
-    static constexpr int RR0 = RP0 + 2 * S::NT;         // [4][n] ratios
-    static constexpr int CL0 = RR0 + 4 * S::N;          // [n] column run starts (int)
-    static constexpr int CN0 = CL0 + S::N;              // [n] column run lengths (int)
-    static constexpr int CSN0 = CN0 + S::N;             // [2][kMaxViews / 4] base view cos, sin
-    static constexpr int FLOATS = CSN0 + 2 * (kMaxViews / 4);
-    static constexpr size_t BYTES = 32 * sizeof(double) + 16 + sizeof(float) * (size_t)FLOATS;
+    static constexpr int RR0 = RP0 + 2 * S::NT;         // [4][n] dx r per view
+    static constexpr int FLOATS = RR0 + 4 * S::N;
+    static constexpr size_t HEAD = 32 * sizeof(double) + 16 * sizeof(int);
+    static constexpr size_t RECS = (HEAD + sizeof(float) * (size_t)FLOATS + 15) / 16 * 16;
+    static constexpr size_t BYTES = RECS + 2 * sizeof(int) * (size_t)S::REC;
+    static_assert(S::REC % 4 == 0, "records are copied in 16-byte pieces");
+    static_assert(BYTES <= 227 * 1024, "shared memory of one CTA");
 };
 
 // The 9-class race-free scatter of the sample buffer into the accumulator
@@ -227,7 +260,7 @@ __device__ __forceinline__ void band_scatter(const float* W, float* Ab, const in
         if (tid < nbc * M) {
             const int b = pb + 3 * (tid % nbc), mm = tid / nbc;
             const int lo = colLo[b], len = colLen[b];
-            const int k1 = lo + ((pk - lo) % 3 + 3) % 3;
+            const int k1 = lo + (pk - lo % 3 + 3) % 3;  // first k >= lo with k = pk (mod 3)
             for (int k = k1 + 3 * mm; k < lo + len; k += 3 * M) {
                 const float g = W[(k - lo) * WP + b];
                 float u, w;
@@ -250,13 +283,14 @@ __global__ void __launch_bounds__(1024, 1) mlem_band_kernel(FusedArgs a) {
     cg::cluster_group cl = cg::this_cluster();
     const int r = (int)cl.block_rank();
     const int hold = blockIdx.x / NB;
-    const int R0 = r * H;
-    const int rows = N - R0 < H ? N - R0 : H;
+    const int R0 = band_start<NB>(r);
+    const int rows = band_start<NB>(r + 1) - R0;
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double* dred = reinterpret_cast<double*>(smem_raw);
-    int* flag = reinterpret_cast<int*>(smem_raw + 32 * sizeof(double));
-    float* sm = reinterpret_cast<float*>(smem_raw + 32 * sizeof(double) + 16);
+    int* flag = reinterpret_cast<int*>(smem_raw + 32 * sizeof(double));  // [0]: hand-over
+    float* sm = reinterpret_cast<float*>(smem_raw + L::HEAD);
+    int* recs = reinterpret_cast<int*>(smem_raw + L::RECS);  // [2][REC]
     float* Fb = sm + L::F0;
     float* Ab = sm + L::A0;
     float* W = sm + L::W0;
@@ -264,9 +298,6 @@ __global__ void __launch_bounds__(1024, 1) mlem_band_kernel(FusedArgs a) {
     float* cpart = sm + L::CP0;
     float* rpart = sm + L::RP0;
     float* rr = sm + L::RR0;
-    int* colLo = reinterpret_cast<int*>(sm + L::CL0);
-    int* colLen = reinterpret_cast<int*>(sm + L::CN0);
-    float* csn = sm + L::CSN0;
 
     const int tid = threadIdx.x;
     const int V = a.V, ngrid = V / 4;
@@ -276,7 +307,6 @@ __global__ void __launch_bounds__(1024, 1) mlem_band_kernel(FusedArgs a) {
     // column mapping: column cb, quarter cq of its run; row mapping per grid
     const int cb = tid % N, cq = tid / N;
 
-    for (int gi = tid; gi < ngrid; gi += NT) view_cos_sin(band_base_view(gi, V), V, &csn[2 * gi], &csn[2 * gi + 1]);
 
     float* tab = a.tab + (size_t)blockIdx.x * ngrid * S::GSTRIDE;
     float* sens = a.sens + (size_t)blockIdx.x * H * N;
@@ -298,40 +328,52 @@ __global__ void __launch_bounds__(1024, 1) mlem_band_kernel(FusedArgs a) {
     const int j_first = m0 < m1 ? job_of(m0) : 0;
     const int j_last = m0 < m1 ? job_of(m1 - 1) : -1;
 
-    // per-grid run bookkeeping of this thread
+    // per-grid run bookkeeping of this thread (row runs: rcnt = 0 if none)
     struct Runs {
-        int clo, ck0, ccnt;            // column run: k = clo + ck0 + s, s < ccnt
-        int kmin, R, T;                // active rows of the band
-        bool ract;
-        int rk, rq, rlo, rb0, rcnt;    // row run: b = rlo + rb0 + s, s < rcnt
+        int clo, ck0, ccnt;      // column run: k = clo + ck0 + s, s < ccnt
+        int rk, rlo, rb0, rcnt;  // row run: row rk, b = rlo + rb0 + s, s < rcnt
     };
-    auto runs_of = [&](const int* rec) -> Runs {
+    // The runs of grid g are staged in shared-memory slot (step parity): the
+    // next grid's record is loaded from global memory during a grid step and
+    // stored into the other slot before that step's last barriers.
+    int rb = 0;  // slot of the current grid step
+    // Start copying grid g's record into slot `slot` (16 bytes per thread,
+    // no registers held); complete with rec_wait() before a barrier.
+    auto rec_copy = [&](int g, int slot) {
+        if (tid < S::REC / 4) {
+            const int* src = geo + (size_t)g * S::REC + 4 * tid;
+            const unsigned dst = (unsigned)__cvta_generic_to_shared(recs + slot * S::REC + 4 * tid);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    auto rec_wait = [&]() { asm volatile("cp.async.wait_all;" ::: "memory"); };
+    // row mapping: thread tid < R T takes row kmin + tid / T, part tid % T
+    auto runs_of = [&](int slot) -> Runs {
         Runs x;
-        const int lo = __ldg(rec + kRecHdr + cb), len = __ldg(rec + kRecHdr + N + cb);
+        const int* h = recs + slot * S::REC;
+        const int* rs = h + kRecHdr;
+        const int lo = rs[cb], len = rs[N + cb];
         const int cS = (len + TC - 1) / TC;
         x.clo = lo;
         x.ck0 = cq * cS;
         x.ccnt = len - x.ck0 < cS ? len - x.ck0 : cS;
         if (x.ccnt < 0) x.ccnt = 0;
-        x.kmin = __ldg(rec + kRecKmin);
-        x.R = __ldg(rec + kRecRows);
-        x.T = __ldg(rec + kRecT);
-        x.ract = x.R > 0 && tid < x.R * x.T;
-        x.rk = x.ract ? x.kmin + tid / x.T : 0;
-        x.rq = x.ract ? tid % x.T : 0;
-        const int rl = x.ract ? __ldg(rec + kRecHdr + 2 * N + x.rk) : 0;
-        const int rn = x.ract ? __ldg(rec + kRecHdr + 3 * N + x.rk) : 0;
-        const int rS = x.ract ? (rn + x.T - 1) / x.T : 0;
+        const int kmin = h[kRecKmin], R = h[kRecRows], T = h[kRecT];
+        const bool ract = R > 0 && tid < R * T;
+        const int rq = ract ? tid % T : 0;
+        x.rk = ract ? kmin + tid / T : 0;
+        const int rl = ract ? rs[2 * N + x.rk] : 0;
+        const int rn = ract ? rs[3 * N + x.rk] : 0;
+        const int rS = ract ? (rn + T - 1) / T : 0;
         x.rlo = rl;
-        x.rb0 = x.rq * rS;
+        x.rb0 = rq * rS;
         x.rcnt = rn - x.rb0 < rS ? rn - x.rb0 : rS;
         if (x.rcnt < 0) x.rcnt = 0;
-        if (tid < N) {
-            colLo[tid] = __ldg(rec + kRecHdr + tid);
-            colLen[tid] = __ldg(rec + kRecHdr + N + tid);
-        }
         return x;
     };
+    rec_copy(0, 0);
+    rec_wait();  // read after the set-up's first barrier
     auto remote = [&](float* p, int rank) -> const float* { return cl.map_shared_rank(p, rank); };
 
     for (int cand = j_last; cand >= j_first; --cand) {
@@ -353,7 +395,7 @@ __global__ void __launch_bounds__(1024, 1) mlem_band_kernel(FusedArgs a) {
             Ab[i] = 0.0f;
         }
         __syncthreads();
-        for (int i = tid; i < (H + 2) * N; i += NT) {
+        for (int i = tid; i < (rows + 2) * N; i += NT) {
             const int l = i / N, j = i % N, gr = R0 - 1 + l;
             if (gr >= 0 && gr < N) Fb[l * P + j + 1] = __ldg(mu + (size_t)gr * N + j);
         }
@@ -362,8 +404,11 @@ __global__ void __launch_bounds__(1024, 1) mlem_band_kernel(FusedArgs a) {
         int buf = 0;
         // ---- attenuation exponents of every grid, sensitivity A^T 1
         for (int gi = 0; gi < ngrid; ++gi) {
-            const float cs = csn[2 * gi], sn = csn[2 * gi + 1];
-            const Runs x = runs_of(geo + (size_t)gi * S::REC);
+            const float cs = __int_as_float(recs[rb * S::REC + kRecCos]);
+            const float sn = __int_as_float(recs[rb * S::REC + kRecSin]);
+            const Runs x = runs_of(rb);
+            const int* colLo = recs + rb * S::REC + kRecHdr;
+            const int* colLen = colLo + N;
             float* Xc = tab + gi * S::GSTRIDE;
             float* XrT = Xc + S::SC * NT;
             float* Uc = XrT + S::SR * NT;
@@ -396,13 +441,15 @@ __global__ void __launch_bounds__(1024, 1) mlem_band_kernel(FusedArgs a) {
                 for (int q2 = 0; q2 < TC; ++q2) tcol += cpart[q2 * N + tid];
                 pb_[tid] = tcol;
             } else if (tid < 2 * N) {
-                const int k = tid - N;
+                const int* h = recs + rb * S::REC;
+                const int k = tid - N, kmin = h[kRecKmin], T = h[kRecT];
                 float trow = 0.0f;
-                if (k >= x.kmin && k < x.kmin + x.R)
-                    for (int q2 = 0; q2 < x.T; ++q2) trow += rpart[(k - x.kmin) * x.T + q2];
+                if (k >= kmin && k < kmin + h[kRecRows])
+                    for (int q2 = 0; q2 < T; ++q2) trow += rpart[(k - kmin) * T + q2];
                 pb_[N + k] = trow;
             }
             cl.sync();
+            rec_copy(gi + 1 < ngrid ? gi + 1 : 0, rb ^ 1);
             {   // columns: suffix along k; bands r' > r lie further along the ray
                 float after = 0.0f, total = 0.0f;
                 for (int q2 = 0; q2 < NB; ++q2) {
@@ -419,14 +466,16 @@ __global__ void __launch_bounds__(1024, 1) mlem_band_kernel(FusedArgs a) {
                 }
                 if (cq == 0) Uc[cb] = ndl * total;
             }
-            if (x.ract) {  // rows: prefix along b; the bands before lie on the side sn points away from
+            if (x.rcnt > 0) {  // rows: prefix along b; the bands before lie on the side sn points away from
+                const int* h = recs + rb * S::REC;
+                const int T = h[kRecT], rq = tid % T, rbase = (x.rk - h[kRecKmin]) * T;
                 float before = 0.0f, total = 0.0f;
                 for (int q2 = 0; q2 < NB; ++q2) {
                     const float v = remote(pb_, q2)[N + x.rk];
                     total += v;
                     if (sn > 0.0f ? q2 < r : q2 > r) before += v;
                 }
-                for (int q2 = 0; q2 < x.rq; ++q2) before += rpart[(x.rk - x.kmin) * x.T + q2];
+                for (int q2 = 0; q2 < rq; ++q2) before += rpart[rbase + q2];
                 float pre = before;
                 for (int s = 0; s < x.rcnt; ++s) {
                     const int b = x.rlo + x.rb0 + s;
@@ -434,9 +483,11 @@ __global__ void __launch_bounds__(1024, 1) mlem_band_kernel(FusedArgs a) {
                     XrT[s * NT + tid] = ndl * (0.5f * m + pre);
                     pre += m;
                 }
-                if (x.rq == 0) Ur[x.rk] = ndl * total;
+                if (rq == 0) Ur[x.rk] = ndl * total;
             }
             buf ^= 1;
+            rec_wait();
+            rb ^= 1;
             __syncthreads();
             {   // G = dx (sum of the grid's four attenuation factors)
                 const float uc = Uc[cb];
@@ -446,7 +497,7 @@ __global__ void __launch_bounds__(1024, 1) mlem_band_kernel(FusedArgs a) {
                 }
             }
             __syncthreads();
-            if (x.ract) {
+            if (x.rcnt > 0) {
                 const float ur = Ur[x.rk];
                 for (int s = 0; s < x.rcnt; ++s) {
                     const int b = x.rlo + x.rb0 + s;
@@ -461,7 +512,7 @@ __global__ void __launch_bounds__(1024, 1) mlem_band_kernel(FusedArgs a) {
         for (int i = tid; i < rows * N; i += NT) {
             const int l = i / N + 1, j = i % N;
             float v = Ab[l * P + j + 1];
-            if (l == 1 && r > 0) v += remote(Ab, r - 1)[(H + 1) * P + j + 1];
+            if (l == 1 && r > 0) v += remote(Ab, r - 1)[(R0 - band_start<NB>(r - 1) + 1) * P + j + 1];
             sens[i] = v;
         }
         // second part of a cut candidate: rank 0 waits for the first part,
@@ -497,7 +548,7 @@ __global__ void __launch_bounds__(1024, 1) mlem_band_kernel(FusedArgs a) {
             Ab[i] = 0.0f;
         }
         __syncthreads();
-        for (int i = tid; i < (H + 2) * N; i += NT) {
+        for (int i = tid; i < (rows + 2) * N; i += NT) {
             const int l = i / N, j = i % N, gr = R0 - 1 + l;
             if (gr >= 0 && gr < N) Fb[l * P + j + 1] = first ? Fc[(size_t)gr * N + j] : __ldcg(Fc + (size_t)gr * N + j);
         }
@@ -509,9 +560,11 @@ __global__ void __launch_bounds__(1024, 1) mlem_band_kernel(FusedArgs a) {
             const bool scoring = (it == Kc);
             if (it == it1 && !(last && a.L)) break;
             for (int gi = 0; gi < ngrid; ++gi) {
-                const float cs = csn[2 * gi], sn = csn[2 * gi + 1];
-                const int* rec = geo + (size_t)gi * S::REC;
-                const Runs x = runs_of(rec);
+                const float cs = __int_as_float(recs[rb * S::REC + kRecCos]);
+                const float sn = __int_as_float(recs[rb * S::REC + kRecSin]);
+                const Runs x = runs_of(rb);
+                const int* colLo = recs + rb * S::REC + kRecHdr;
+                const int* colLen = colLo + N;
                 const float* Xc = tab + gi * S::GSTRIDE;
                 const float* XrT = Xc + S::SC * NT;
                 const float* Uc = XrT + S::SR * NT;
@@ -546,7 +599,7 @@ __global__ void __launch_bounds__(1024, 1) mlem_band_kernel(FusedArgs a) {
                 __syncthreads();
                 {   // forward, row views: the samples back from W
                     float acc3 = 0.0f, acc4 = 0.0f;
-                    if (x.ract) {
+                    if (x.rcnt > 0) {
                         const float ur = Ur[x.rk];
                         for (int s = 0; s < x.rcnt; ++s) {
                             const int b = x.rlo + x.rb0 + s;
@@ -570,20 +623,22 @@ __global__ void __launch_bounds__(1024, 1) mlem_band_kernel(FusedArgs a) {
                     pb_[tid] = p1;
                     pb_[N + tid] = p2;
                 } else if (tid < 2 * N) {
-                    const int k = tid - N;
+                    const int* h = recs + rb * S::REC;
+                    const int k = tid - N, kmin = h[kRecKmin], T = h[kRecT];
                     float p3 = 0.0f, p4 = 0.0f;
-                    if (k >= x.kmin && k < x.kmin + x.R) {
-                        for (int q2 = 0; q2 < x.T; ++q2) {
-                            p3 += rpart[(k - x.kmin) * x.T + q2];
-                            p4 += rpart[NT + (k - x.kmin) * x.T + q2];
+                    if (k >= kmin && k < kmin + h[kRecRows]) {
+                        for (int q2 = 0; q2 < T; ++q2) {
+                            p3 += rpart[(k - kmin) * T + q2];
+                            p4 += rpart[NT + (k - kmin) * T + q2];
                         }
                     }
                     pb_[2 * N + k] = p3;
                     pb_[3 * N + k] = p4;
                 }
                 cl.sync();
+                rec_copy(gi + 1 < ngrid ? gi + 1 : 0, rb ^ 1);
                 {   // q = dx * (sum of the bands' partials, rank order), then
-                    // r = S / q, or the Eq. 5 terms (rank 0) when scoring
+                    // dx r = dx S / q, or the Eq. 5 terms (rank 0) when scoring
                     const int vs = tid / N, j = tid % N;
                     float q = 0.0f;
                     for (int q2 = 0; q2 < NB; ++q2) q += remote(pb_, q2)[tid];
@@ -594,24 +649,26 @@ __global__ void __launch_bounds__(1024, 1) mlem_band_kernel(FusedArgs a) {
                     if (scoring) {
                         if (r == 0) lacc += loglik_term(Sv, q, a.include_lgamma);
                     } else {
-                        rr[tid] = q > 0.0f ? Sv / q : 0.0f;
+                        rr[tid] = q > 0.0f ? dx * (Sv / q) : 0.0f;
                     }
                 }
                 buf ^= 1;
+                rec_wait();
+                rb ^= 1;
                 __syncthreads();
                 if (scoring) continue;
                 {   // back-projection weights, column views
                     const float uc = Uc[cb];
-                    const float r1 = dx * rr[cb], r2 = dx * rr[N + cb];
+                    const float r1 = rr[cb], r2 = rr[N + cb];
                     for (int s = 0; s < x.ccnt; ++s) {
                         const float y = Xc[s * NT + tid];
                         W[(x.ck0 + s) * WP + cb] = fmaf(ex2(y), r1, ex2(uc - y) * r2);
                     }
                 }
                 __syncthreads();
-                if (x.ract) {  // row views
+                if (x.rcnt > 0) {  // row views
                     const float ur = Ur[x.rk];
-                    const float r3 = dx * rr[2 * N + x.rk], r4 = dx * rr[3 * N + x.rk];
+                    const float r3 = rr[2 * N + x.rk], r4 = rr[3 * N + x.rk];
                     for (int s = 0; s < x.rcnt; ++s) {
                         const int b = x.rlo + x.rb0 + s;
                         const float y = XrT[s * NT + tid];
@@ -628,13 +685,13 @@ __global__ void __launch_bounds__(1024, 1) mlem_band_kernel(FusedArgs a) {
             for (int i = tid; i < rows * N; i += NT) {
                 const int l = i / N + 1, j = i % N, pi = l * P + j + 1;
                 float acc = Ab[pi];
-                if (l == 1 && r > 0) acc += remote(Ab, r - 1)[(H + 1) * P + j + 1];
+                if (l == 1 && r > 0) acc += remote(Ab, r - 1)[(R0 - band_start<NB>(r - 1) + 1) * P + j + 1];
                 const float sv = sens[i];
                 Fb[pi] = sv > 0.0f ? Fb[pi] * acc / sv : 0.0f;
             }
             cl.sync();
             if (r < NB - 1)
-                for (int j = tid; j < N; j += NT) Fb[(H + 1) * P + j + 1] = remote(Fb, r + 1)[P + j + 1];
+                for (int j = tid; j < N; j += NT) Fb[(rows + 1) * P + j + 1] = remote(Fb, r + 1)[P + j + 1];
             for (int i = tid; i < BIMG; i += NT) Ab[i] = 0.0f;
             __syncthreads();
         }
