@@ -306,10 +306,13 @@ __global__ void __launch_bounds__(NT, (fused_min_blocks<N, NT>())) mlem_fused_ke
                 }
                 const int vc1 = gi, vc2 = gi + V / 2;           // column views
                 const int vr1 = gi + V / 4, vr2 = gi + 3 * V / 4;  // row views (QUAD)
-                // forward, column views: sample F on the grid
+                // forward, column views: sample F on the grid.  (The column
+                // and row passes and the column weights unroll by 8: fully
+                // unrolled they spill at 64 registers; measured +7.8 %.)
                 {
                     const float uc = Uc[lb];
                     float acc1 = 0.0f, acc2 = 0.0f;
+#pragma unroll 8
                     for (int s = 0; s < SEG; ++s) {
                         const int k = k0 + s;
                         float u, w;
@@ -327,6 +330,7 @@ __global__ void __launch_bounds__(NT, (fused_min_blocks<N, NT>())) mlem_fused_ke
                     __syncthreads();
                     const float ur = Ur[lb];
                     float acc3 = 0.0f, acc4 = 0.0f;
+#pragma unroll 8
                     for (int s = 0; s < SEG; ++s) {
                         const int b = k0 + s;
                         const float f = W[lb * WP + b];
@@ -367,6 +371,7 @@ __global__ void __launch_bounds__(NT, (fused_min_blocks<N, NT>())) mlem_fused_ke
                 {
                     const float uc = Uc[lb];
                     const float r1 = dx * rr[lb], r2 = dx * rr[N + lb];
+#pragma unroll 8
                     for (int s = 0; s < SEG; ++s) {
                         const int k = k0 + s;
                         const float y = Xc[k * N + lb];
