@@ -219,9 +219,10 @@ int boac_mlem_ragged(const boac_geom *classes, int n_classes,
  * every GPU that loads the library keeps until the process exits.
  *   - The first call on a device looks up that array's device address
  *     (cudaGetSymbolAddress); make that first call before any stream capture.
- *   - Fewer candidates run at once when one slot's scratch (n_views * n^2 + n^2
- *     floats) does not fit 64 MiB many times; BOAC_EWORKSPACE if not even one
- *     fits (not possible for the supported sizes, n <= 128 and n_views <= 720).
+ *   - Fewer candidates run at once when one slot's scratch (about
+ *     n_views * n^2 / 2 + n^2 floats, plus three 256 x 257 images at n = 256)
+ *     does not fit 64 MiB many times; BOAC_EWORKSPACE if not even one fits
+ *     (never for n <= 128; at n = 256 above about 500 views).
  *   - Every call shares the one array: calls that can overlap on the GPU
  *     (different streams, or other threads) race and corrupt each other's
  *     results.  Serialise them.  Nothing needs to start at zero: each call
