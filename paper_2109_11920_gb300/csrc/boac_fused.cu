@@ -177,6 +177,7 @@ __global__ void __launch_bounds__(NT, (fused_min_blocks<N, NT>())) mlem_fused_ke
         __syncthreads();
 
         // ---- system matrix (attenuation exponents) + sensitivity A^T 1
+        // (loops unrolled by 8, as in the iterations below: +0.8 % measured)
         for (int gi = 0; gi < ngrid; ++gi) {
             const float cs = csn[2 * gi], sn = csn[2 * gi + 1];
             float* Xc = tab + gi * gstride;
@@ -184,6 +185,7 @@ __global__ void __launch_bounds__(NT, (fused_min_blocks<N, NT>())) mlem_fused_ke
             float* Uc = QUAD ? Xc + 2 * NN : Xc + NN;
             float* Ur = Uc + N;
             float ps = 0.0f;
+#pragma unroll 8
             for (int s = 0; s < SEG; ++s) {
                 float u, w;
                 sample_uw(k0 + s, lb, cs, sn, c, &u, &w);
@@ -202,6 +204,7 @@ __global__ void __launch_bounds__(NT, (fused_min_blocks<N, NT>())) mlem_fused_ke
                     if (s2 > seg) after += v;
                 }
                 float suf = after;
+#pragma unroll 8
                 for (int s = SEG - 1; s >= 0; --s) {
                     const int k = k0 + s;
                     const float m = W[k * WP + lb];
@@ -212,6 +215,7 @@ __global__ void __launch_bounds__(NT, (fused_min_blocks<N, NT>())) mlem_fused_ke
             }
             if (QUAD) {  // rows: prefix sums from b = 0
                 float pr = 0.0f;
+#pragma unroll 8
                 for (int s = 0; s < SEG; ++s) pr += W[lb * WP + k0 + s];
                 redr[seg * N + lb] = pr;
                 __syncthreads();
@@ -223,6 +227,7 @@ __global__ void __launch_bounds__(NT, (fused_min_blocks<N, NT>())) mlem_fused_ke
                     if (s2 < seg) before += v;
                 }
                 float pre = before;
+#pragma unroll 8
                 for (int s = 0; s < SEG; ++s) {
                     const int b = k0 + s;
                     const float m = W[lb * WP + b];
@@ -234,6 +239,7 @@ __global__ void __launch_bounds__(NT, (fused_min_blocks<N, NT>())) mlem_fused_ke
             __syncthreads();
             {   // G = dx (sum of the grid's views' attenuation factors)
                 const float uc = Uc[lb];
+#pragma unroll 8
                 for (int s = 0; s < SEG; ++s) {
                     const int k = k0 + s;
                     const float y = Xc[k * N + lb];
@@ -243,6 +249,7 @@ __global__ void __launch_bounds__(NT, (fused_min_blocks<N, NT>())) mlem_fused_ke
             if (QUAD) {
                 __syncthreads();
                 const float ur = Ur[lb];
+#pragma unroll 8
                 for (int s = 0; s < SEG; ++s) {
                     const int b = k0 + s;
                     const float y = XrT[b * N + lb];
