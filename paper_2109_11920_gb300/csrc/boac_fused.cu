@@ -350,27 +350,17 @@ __global__ void __launch_bounds__(NT, (fused_min_blocks<N, NT>())) mlem_fused_ke
                 }
                 __syncthreads();
                 // q, then r = S / q (or the Eq. 5 terms when scoring)
-                if (tid < (QUAD ? 2 * N : N)) {
-                    const int j = tid % N;
-                    const bool row = tid >= N;
-                    const float* rp = row ? redr : redc;
-                    float q1 = 0.0f, q2 = 0.0f;
+                for (int t = tid; t < (QUAD ? 4 * N : 2 * N); t += NT) {  // one ray per thread
+                    const int j = t % N, vi = t / N;  // views vc1, vc2, vr1, vr2
+                    const float* rp = (vi >= 2 ? redr : redc) + ((vi & 1) ? NSEG * N : 0);
+                    float q = 0.0f;
 #pragma unroll
-                    for (int s2 = 0; s2 < NSEG; ++s2) {
-                        q1 += rp[s2 * N + j];
-                        q2 += rp[(NSEG + s2) * N + j];
-                    }
-                    q1 *= dx;
-                    q2 *= dx;
-                    const int v1 = row ? vr1 : vc1, v2 = row ? vr2 : vc2;
-                    const float S1 = __ldg(S + (size_t)v1 * N + j);
-                    const float S2 = __ldg(S + (size_t)v2 * N + (N - 1 - j));
-                    if (scoring) {
-                        lacc += loglik_term(S1, q1, a.include_lgamma) + loglik_term(S2, q2, a.include_lgamma);
-                    } else {
-                        rr[(row ? 2 : 0) * N + j] = q1 > 0.0f ? S1 / q1 : 0.0f;
-                        rr[(row ? 3 : 1) * N + j] = q2 > 0.0f ? S2 / q2 : 0.0f;
-                    }
+                    for (int s2 = 0; s2 < NSEG; ++s2) q += rp[s2 * N + j];
+                    q *= dx;
+                    const int v = vi == 0 ? vc1 : vi == 1 ? vc2 : vi == 2 ? vr1 : vr2;
+                    const float Sv = __ldg(S + (size_t)v * N + ((vi & 1) ? N - 1 - j : j));
+                    if (scoring) lacc += loglik_term(Sv, q, a.include_lgamma);
+                    else rr[vi * N + j] = q > 0.0f ? Sv / q : 0.0f;
                 }
                 __syncthreads();
                 if (scoring) continue;
