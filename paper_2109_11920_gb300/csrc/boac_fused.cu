@@ -103,7 +103,6 @@ __global__ void __launch_bounds__(NT, (fused_min_blocks<N, NT>())) mlem_fused_ke
     constexpr int P = Lay::P, IMG = Lay::IMG, NN = Lay::NN, WP = Lay::WP;
     constexpr int NSEG = Lay::NSEG, SEG = Lay::SEG;
     constexpr float kLog2e = 1.44269504088896340736f;
-    static_assert(!QUAD || NT >= 2 * N, "row views need 2N threads in the ratio step");
 
     extern __shared__ __align__(16) float smem[];
     float* const img_base = fused_global_images(N)
