@@ -267,7 +267,7 @@ extern "C" int boac_score_grad(const boac_geom* g, const boac_tissue* t, const f
 
     // one MLEM step F_in -> F_out, leaving q, r and z = A^T r behind
     auto mlem_step = [&](const float* F_in, float* F_o, float* q, float* r, float* z) {
-        project_table_kernel<<<rg, kRayThreads, 0, st>>>(n, V, dx, tab, F_in, q);
+        project_table(g, B, tab, F_in, dx, q, st);
         ratio_batched_kernel<<<g1b, 256, 0, st>>>(B, (int)vb, S, s_stride, q, r);
         backproject_table(g, B, tab, r, dx, z, 0, partial, st);
         cudaMemcpyAsync(F_o, F_in, sizeof(float) * cnt_pix, cudaMemcpyDeviceToDevice, st);
@@ -302,7 +302,7 @@ extern "C" int boac_score_grad(const boac_geom* g, const boac_tissue* t, const f
         if (K == 0) cudaMemcpyAsync(Fk, ck, sizeof(float) * cnt_pix, cudaMemcpyDeviceToDevice, st);
     }
     // ---- score and d L / d q^K
-    project_table_kernel<<<rg, kRayThreads, 0, st>>>(n, V, dx, tab, Fk, qK);
+    project_table(g, B, tab, Fk, dx, qK, st);
     loglik_kernel<<<B, 256, 0, st>>>((int)vb, qK, S, s_stride, include_lgamma, L);
     if (F_out) cudaMemcpyAsync(F_out, Fk, sizeof(float) * cnt_pix, cudaMemcpyDeviceToDevice, st);
     qbar_final_kernel<<<g1b, 256, 0, st>>>(B, (int)vb, S, s_stride, qK, qbar);
@@ -325,7 +325,7 @@ extern "C" int boac_score_grad(const boac_geom* g, const boac_tissue* t, const f
             const float* r = rseg + (size_t)tt * B * vb;
             const float* z = zseg + (size_t)tt * B * nn;
             mlem_step_adjoint_kernel<<<g1p, 256, 0, st>>>(cnt_pix, Fbar, Fn, Fn1, z, sens, zbar, sensbar, Fnew);
-            project_table_kernel<<<rg, kRayThreads, 0, st>>>(n, V, dx, tab, zbar, rbar);
+            project_table(g, B, tab, zbar, dx, rbar, st);
             qbar_step_kernel<<<g1b, 256, 0, st>>>(B, (int)vb, S, s_stride, q, rbar, qbar);
             backproject_table(g, B, tab, qbar, dx, Fnew, 1, partial, st);
             abar_accum_kernel<<<rg, kRayThreads, 0, st>>>(n, V, dx, r, zbar, qbar, Fn, abar);

@@ -269,13 +269,13 @@ extern "C" int boac_mlem_plain(const boac_geom* g, const float* mu, const float*
         int s = backproject_table(g, 1, tab, nullptr, dx, sens, 0, partial, st);
         if (s != BOAC_OK) return s;
         for (int it = 0; it < K; ++it) {
-            project_table_kernel<<<ray_grid(g, 1), kRayThreads, 0, st>>>(n, V, dx, tab, F_c, q);
+            project_table(g, 1, tab, F_c, dx, q, st);
             ratio_kernel<<<grid_1d((long long)vb, 256), 256, 0, st>>>((int)vb, S_c, q, r);
             backproject_table(g, 1, tab, r, dx, bp, 0, partial, st);
             update_kernel<<<grid_1d((long long)nn, 256), 256, 0, st>>>((int)nn, F_c, bp, sens);
         }
         if (L) {
-            project_table_kernel<<<ray_grid(g, 1), kRayThreads, 0, st>>>(n, V, dx, tab, F_c, q);
+            project_table(g, 1, tab, F_c, dx, q, st);
             loglik_kernel<<<1, 256, 0, st>>>((int)vb, q, S_c, 0, include_lgamma, L + cand);
         }
         s = launch_status();

@@ -37,6 +37,11 @@ int grid_1d(long long count, int threads);
 // floats), or the per-pixel gather where the geometry has no grouped kernel
 // (then `partial` may be null).
 size_t bp_partial_floats(const boac_geom* g, int B);
+// q[cand][v][bin] = dx * sum_k tab_v[k][bin] F(sample (k, bin) of view v) for
+// B candidates (boac_bpgroup.cu): one CTA per candidate and sample grid with
+// F in shared memory, or one thread per ray where no grouped kernel exists.
+int project_table(const boac_geom* g, int B, const float* tab, const float* F, float dx, float* q,
+                  cudaStream_t st);
 int backproject_table(const boac_geom* g, int B, const float* tab, const float* y, float scale, float* out,
                       int accumulate, float* partial, cudaStream_t st);
 
