@@ -100,3 +100,16 @@ def test_zero_iterations_and_lone_candidate(cuda):
     assert torch.equal(F, F0)
     Lo = oracle.loglik(p.S, oracle.project(p.geom, p.mu[0], np.full((256, 256), 0.5)))
     assert abs(float(L[0]) - Lo) < 1e-6 * abs(Lo)
+
+
+def test_largest_view_count(cuda):
+    """720 views (the library's maximum): 180 sample grids per iteration,
+    the largest exponent table per CTA."""
+    p = make_problem(256, 0.1, 720, 1e6, B=1, seed=51)
+    g = Geom.make(p.n, p.dx, p.V)
+    mu = torch.tensor(p.mu, dtype=torch.float32, device=cuda)
+    S = torch.tensor(p.S, dtype=torch.float32, device=cuda)
+    F, L = boac.boac_mlem(g, mu, S, torch.ones(1, 256, 256, device=cuda), 2)
+    Fo, Lo, _ = oracle.mlem_batch(p.geom, p.mu, p.S, 2)
+    assert rel_l2(F[0].cpu().numpy(), Fo[0]) < 1e-4
+    assert abs(float(L[0]) - Lo[0]) < 1e-6 * abs(Lo[0])

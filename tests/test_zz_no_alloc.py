@@ -59,3 +59,17 @@ def test_noalloc_matches_workspace_entry_point(cuda):
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     assert lib.boac_mlem_noalloc(ctypes.byref(bad), _p(mu_all), _p(S), 0, _p(F), 2, 20, _p(L), 1,
                                  stream) == _lib.BOAC_EINVAL
+
+
+def test_noalloc_rejects_problems_beyond_its_scratch(cuda):
+    """At 256 x 256 with 720 views one candidate's scratch (about 95 MB) does
+    not fit the built-in 64 MiB: the call fails with BOAC_EWORKSPACE before
+    launching anything."""
+    lib = _lib.load()
+    g = Geom.make(256, 0.1, 720)
+    mu = torch.zeros(1, 256, 256, device=cuda)
+    S = torch.zeros(720, 256, device=cuda)
+    F = torch.ones(1, 256, 256, device=cuda)
+    L = torch.empty(1, dtype=torch.float64, device=cuda)
+    assert call_noalloc(lib, g, mu, S, F, 2, L) == _lib.BOAC_EWORKSPACE
+    assert torch.equal(F, torch.ones_like(F))
