@@ -1,0 +1,99 @@
+"""Geometry the 256 x 256 cluster kernel relies on, checked on the CPU with
+float32 arithmetic emulated in numpy: every ray sample inside the image
+belongs to exactly one band; within a band the samples of a lattice column
+(a ray of the base view) form one run of consecutive k and those of a
+lattice row one run of consecutive b; runs and per-thread steps fit the
+kernel's buffers (constants restated from boac_band.cu's shapes).  The
+kernel's record kernel checks the same at run time and refuses to run
+otherwise; this test pins the reasoning behind the buffer sizes."""
+import math
+
+import numpy as np
+import pytest
+
+N, NT = 256, 1024
+F32 = np.float32
+
+
+def band_starts(nb):
+    if nb == 5:
+        return [0, 52, 103, 152, 203, 256]
+    h = -(-N // nb)
+    return [min(r * h, N) for r in range(nb + 1)]
+
+
+def shape(nb):
+    st = band_starts(nb)
+    H = max(st[r + 1] - st[r] for r in range(nb))
+    LC = ((H + 1) * 141422 + 99999) // 100000 + 2
+    TC = NT // N
+    return H, LC, (LC + TC - 1) // TC, (LC + 1) // 2
+
+
+def cos_sin(v, V):
+    """Quadrant exact, in-quadrant angle in float64 rounded once (as the kernels)."""
+    quad = (4 * v // V) % 4
+    th = 1.5707963267948966192 * ((4 * v) % V) / V
+    c, s = F32(math.cos(th)), F32(math.sin(th))
+    return [(c, s), (-s, c), (-c, -s), (s, -c)][quad]
+
+
+def fma32(a, b, c):
+    # a * b is exact in float64 for float32 operands; one rounding to float32
+    return (a.astype(np.float64) * np.float64(b) + c.astype(np.float64)).astype(F32)
+
+
+def sample_uw(cs, sn):
+    c = F32(0.5 * (N - 1))
+    K, B = np.meshgrid(np.arange(N), np.arange(N), indexing="ij")
+    kc = (K.astype(F32) - c).astype(F32)
+    bc = (B.astype(F32) - c).astype(F32)
+    u = fma32(-kc, sn, fma32(bc, cs, np.full_like(bc, c)))
+    w = fma32(kc, cs, fma32(bc, sn, np.full_like(bc, c)))
+    return u, w
+
+
+def runs(mask, axis):
+    """Lengths of the runs along `axis`; asserts each line holds one run."""
+    m = np.moveaxis(mask, axis, 0)
+    lens = m.sum(0)
+    first = np.argmax(m, axis=0)
+    last = m.shape[0] - 1 - np.argmax(m[::-1], axis=0)
+    nz = lens > 0
+    assert np.all(last[nz] - first[nz] + 1 == lens[nz]), "a line's samples are not one run"
+    return lens
+
+
+@pytest.mark.parametrize("nb", [5, 6, 8])
+@pytest.mark.parametrize("V,grids", [(16, None), (180, None), (720, range(0, 180, 7))])
+def test_band_runs_fit_the_kernel_buffers(nb, V, grids):
+    st = band_starts(nb)
+    H, LC, SC, SR = shape(nb)
+    for gi in (grids if grids is not None else range(V // 4)):
+        base = gi if 8 * gi <= V else gi + 3 * V // 4
+        cs, sn = cos_sin(base % V, V)
+        assert cs > 0.7  # base angle within (-45, 45] degrees
+        u, w = sample_uw(cs, sn)
+        inside = (u > -1) & (u < N) & (w > -1) & (w < N)
+        fi = np.floor(w).astype(int)
+        band = np.searchsorted(np.array(st[1:-1]), fi, side="right")
+        total = 0
+        for r in range(nb):
+            m = inside & (band == r)
+            total += int(m.sum())
+            col = runs(m, 0)  # along k for every b
+            row = runs(m, 1)  # along b for every k
+            assert col.max() <= LC
+            assert int(np.max(-(-col // (NT // N)))) <= SC
+            active = np.nonzero(row)[0]
+            if len(active):
+                R = active[-1] - active[0] + 1
+                T = NT // R
+                assert int(np.max(-(-row // T))) <= SR
+        assert total == int(inside.sum())  # each inside sample in exactly one band
+
+
+def test_band_heights_fill_the_image():
+    for nb in (5, 6, 8):
+        st = band_starts(nb)
+        assert st[0] == 0 and st[-1] == N and all(b > a for a, b in zip(st, st[1:]))
