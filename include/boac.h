@@ -126,13 +126,16 @@ int boac_project(const boac_geom *g, const float *mu, const float *F, int B,
                  float *q, void *stream);
 
 /* ---- Eq. 2 adjoint: out = (A^mu)^T y -----------------------------------
- * Exact transpose of boac_project (same bilinear weights), computed as a
- * gather so that the result is deterministic.
+ * Exact transpose of boac_project (same bilinear weights), deterministic:
+ * for n = 64, 96, 128 with an even view count a race-free scatter of the
+ * views that share a sample grid into per-grid images summed in grid order,
+ * for other sizes a per-pixel gather.
  *   y   [B][n_views][n_bins] (device, float32); NULL means y = 1 everywhere
  *       (the MLEM sensitivity image)
  *   out [B][n][n]            output (device, float32)
  *   ws  workspace of boac_workspace_bytes(g, B, BOAC_OP_BACKPROJECT) bytes
- *       (holds the attenuation factors of every ray sample). */
+ *       (holds the attenuation factors of every ray sample and the per-grid
+ *       images). */
 int boac_backproject(const boac_geom *g, const float *mu, const float *y,
                      int B, float *out, void *ws, size_t ws_bytes,
                      void *stream);
@@ -151,7 +154,9 @@ int boac_backproject(const boac_geom *g, const float *mu, const float *y,
  *   K        iterations (>= 0)
  *   L        [B] float64 output, or NULL to skip the score
  * boac_mlem is the batched path: one persistent fused kernel runs every
- * iteration of every candidate on chip.  boac_mlem_plain is the
+ * iteration of every candidate on chip (n <= 128: one CTA per candidate;
+ * n = 256 with n_views % 4 == 0: a thread-block cluster per candidate, the
+ * image split into bands of rows over its CTAs).  boac_mlem_plain is the
  * launch-per-step path: one candidate at a time, separate project / ratio /
  * backproject / update kernels per iteration (the comparison baseline).
  * Workspace: boac_workspace_bytes(g, B, BOAC_OP_MLEM / BOAC_OP_MLEM_PLAIN). */
@@ -174,8 +179,13 @@ int boac_mlem_plain(const boac_geom *g, const float *mu, const float *S,
  * first.  config[c] (host array, or NULL for defaults) picks class c's launch
  * shape: 2 * shape + pair, shape 0/1/2 = CTAs of 2n/4n/8n (<= 1024) threads,
  * pair = 1 for two views per sample grid instead of four (four needs
- * n_views % 4 == 0); the autotuner of the Python package chooses them.
- *   classes  [n_classes] geometries (host), 1 <= n_classes <= 8, sides 64/96/128
+ * n_views % 4 == 0); for n = 256 with n_views % 4 == 0, configurations 6, 7
+ * and 8 run each candidate on a thread-block cluster of 5, 6 or 8 CTAs that
+ * split the image into bands of rows (the default there: the cluster size
+ * that keeps the most SMs busy).  An id that does not apply to a class is
+ * BOAC_EINVAL.  The autotuner of the Python package chooses them.
+ *   classes  [n_classes] geometries (host), 1 <= n_classes <= 8, sides
+ *            64/96/128/256
  *   cands    [B] descriptors (host)
  *   ws       boac_mlem_ragged_workspace_bytes(...) bytes (device)
  * boac_mlem_ragged = boac_mlem_ragged_prepare (sorts the candidates and
