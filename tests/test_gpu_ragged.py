@@ -107,3 +107,31 @@ def test_ragged_full_size_sampled(cuda):
         Fo, Lo, _ = oracle.mlem_batch(p.geom, p.mu, p.S, int(K[b]))
         assert rel_l2(batch.image(b).cpu().numpy(), Fo[0]) < 1e-4, (c, b)
         assert abs(L[b] - Lo[0]) < 1e-6 * abs(Lo[0]), (c, b)
+
+
+def test_ragged_mixes_one_cta_and_cluster_classes(cuda):
+    """A 128 x 128 class (one CTA per candidate) and a 256 x 256 class (a
+    cluster of CTAs per candidate) in one call and one workspace: every
+    candidate equals the uniform entry point bit for bit, and one per class
+    the oracle."""
+    classes = [(128, 0.2, 120), (256, 0.1, 16)]
+    cls = [1, 0, 1, 0, 0, 1, 1]
+    K = [3, 4, 2, 2, 5, 1, 4]
+    probs = [make_problem(*classes[c], counts=2e5, B=1, seed=400 + i) for i, c in enumerate(cls)]
+    geoms = [Geom.make(n, float(np.float32(dx)), V) for n, dx, V in classes]
+    mu = [torch.tensor(p.mu[0], dtype=torch.float32, device=cuda) for p in probs]
+    S = [torch.tensor(p.S, dtype=torch.float32, device=cuda) for p in probs]
+    batch = boac.RaggedBatch(geoms, cls, K, mu, S, device=cuda)
+    L = boac.boac_mlem_ragged(batch).cpu().numpy()
+    for b, p in enumerate(probs):
+        g = geoms[cls[b]]
+        F, Lu = boac.boac_mlem(g, torch.tensor(p.mu, dtype=torch.float32, device=cuda),
+                               torch.tensor(p.S, dtype=torch.float32, device=cuda),
+                               torch.ones(1, p.n, p.n, device=cuda), K[b])
+        torch.testing.assert_close(batch.image(b), F[0], rtol=0, atol=0)
+        assert L[b] == float(Lu[0])
+    for b in (1, 0):
+        p = probs[b]
+        Fo, Lo, _ = oracle.mlem_batch(p.geom, p.mu, p.S, K[b])
+        assert rel_l2(batch.image(b).cpu().numpy(), Fo[0]) < 1e-4
+        assert abs(L[b] - Lo[0]) < 1e-6 * abs(Lo[0])
