@@ -620,11 +620,6 @@ static int variant_holders(const boac_geom* g, const FusedVariant* v, int B) {
     return (int)(h < B ? h : B);
 }
 
-int fused_slots(const boac_geom* g, int B) {
-    const FusedVariant* v = get_variant(g, default_config(g));
-    return v ? variant_holders(g, v, B) : 0;
-}
-
 size_t fused_workspace_bytes(const boac_geom* g, int B) {
     const FusedVariant* v = get_variant(g, default_config(g));
     const int h = v ? variant_holders(g, v, B) : 0;

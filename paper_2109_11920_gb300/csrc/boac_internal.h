@@ -35,8 +35,7 @@ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 size_t plain_candidate_bytes(const boac_geom* g);
 size_t backproject_candidate_bytes(const boac_geom* g);
 
-// Fused MLEM: resident CTA slots and workspace for geometry g and B candidates.
-int fused_slots(const boac_geom* g, int B);
+// Fused MLEM: workspace for geometry g and B candidates.
 size_t fused_workspace_bytes(const boac_geom* g, int B);
 
 }  // namespace boac
