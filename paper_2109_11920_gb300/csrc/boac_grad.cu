@@ -57,6 +57,84 @@ __global__ void abar_accum_kernel(int n, int V, float dx, const float* __restric
     }
 }
 
+// The same accumulation, one CTA per (candidate, sample grid), X1 and X2
+// sampled through L1 as in the per-ray kernel but once per grid point for
+// the grid's views: a column pass for views phi (table entry (k, b)) and
+// phi + pi ((n-1-k, n-1-b)), a row pass for phi + pi/2 ((n-1-b, k)) and
+// phi + 3pi/2 ((b, n-1-k)), every table access coalesced.
+template <int N, int NT, bool QUAD>
+__global__ void __launch_bounds__(NT) abar_grid_kernel(int V, float dx, const float* __restrict__ y1,
+                                                      const float* __restrict__ X1, const float* __restrict__ y2,
+                                                      const float* __restrict__ X2, float* __restrict__ abar) {
+    constexpr int NSEG = NT / N, SEG = N / NSEG;
+    static_assert(NT % N == 0 && N % NSEG == 0, "segmentation");
+    const int gi = blockIdx.x, cand = blockIdx.y;
+    const int tid = threadIdx.x, lb = tid % N, k0 = (tid / N) * SEG;
+    const size_t nn = (size_t)N * N, vb = (size_t)V * N;
+    const float* x1 = X1 + cand * nn;
+    const float* x2 = X2 ? X2 + cand * nn : nullptr;
+    float cs, sn;
+    view_cos_sin(gi, V, &cs, &sn);
+    const float c = 0.5f * (float)(N - 1);
+    auto wt = [&](const float* y, int v, int bin) {
+        return dx * (y ? __ldg(y + cand * vb + (size_t)v * N + bin) : 1.0f);
+    };
+    float* ab = abar + (size_t)cand * V * nn;
+    {   // columns: views phi and phi + pi
+        const int v1 = gi, v2 = gi + V / 2;
+        const float w11 = wt(y1, v1, lb), w12 = wt(y1, v2, N - 1 - lb);
+        const float w21 = x2 ? wt(y2, v1, lb) : 0.0f, w22 = x2 ? wt(y2, v2, N - 1 - lb) : 0.0f;
+        float* a1 = ab + (size_t)v1 * nn;
+        float* a2 = ab + (size_t)v2 * nn;
+        for (int s = 0; s < SEG; ++s) {
+            const int k = k0 + s;
+            float u, w;
+            sample_uw(k, lb, cs, sn, c, &u, &w);
+            const float f1 = bilerp_global(x1, N, u, w);
+            const float f2 = x2 ? bilerp_global(x2, N, u, w) : 0.0f;
+            a1[(size_t)k * N + lb] += fmaf(w21, f2, w11 * f1);
+            a2[(size_t)(N - 1 - k) * N + (N - 1 - lb)] += fmaf(w22, f2, w12 * f1);
+        }
+    }
+    if (QUAD) {  // rows: views phi + pi/2 and phi + 3pi/2
+        const int v3 = gi + V / 4, v4 = gi + 3 * V / 4, k = lb;
+        const float w13 = wt(y1, v3, k), w14 = wt(y1, v4, N - 1 - k);
+        const float w23 = x2 ? wt(y2, v3, k) : 0.0f, w24 = x2 ? wt(y2, v4, N - 1 - k) : 0.0f;
+        float* a3 = ab + (size_t)v3 * nn;
+        float* a4 = ab + (size_t)v4 * nn;
+        for (int s = 0; s < SEG; ++s) {
+            const int b = k0 + s;
+            float u, w;
+            sample_uw(k, b, cs, sn, c, &u, &w);
+            const float f1 = bilerp_global(x1, N, u, w);
+            const float f2 = x2 ? bilerp_global(x2, N, u, w) : 0.0f;
+            a3[(size_t)(N - 1 - b) * N + k] += fmaf(w23, f2, w13 * f1);
+            a4[(size_t)b * N + (N - 1 - k)] += fmaf(w24, f2, w14 * f1);
+        }
+    }
+}
+
+// abar += dx (y1 (B X1) + y2 (B X2)) for B candidates: per grid for image
+// sides 64, 96, 128 and even view counts, else one thread per ray.
+static int abar_accum(const boac_geom* g, int B, float dx, const float* y1, const float* X1, const float* y2,
+                      const float* X2, float* abar, cudaStream_t st) {
+    const int n = g->n, V = g->n_views;
+    if (!((n == 64 || n == 96 || n == 128) && V % 2 == 0)) {
+        abar_accum_kernel<<<ray_grid(g, B), kRayThreads, 0, st>>>(n, V, dx, y1, X1, y2, X2, abar);
+        return launch_status();
+    }
+    const bool quad = V % 4 == 0;
+    const dim3 grid(quad ? V / 4 : V / 2, B);
+#define X(NV, TV)                                                                                   \
+    if (n == NV) {                                                                                  \
+        if (quad) abar_grid_kernel<NV, TV, true><<<grid, TV, 0, st>>>(V, dx, y1, X1, y2, X2, abar);  \
+        else abar_grid_kernel<NV, TV, false><<<grid, TV, 0, st>>>(V, dx, y1, X1, y2, X2, abar);      \
+    }
+    X(64, 256) X(96, 384) X(128, 512)
+#undef X
+    return launch_status();
+}
+
 // In place: abar -> mbar_k = -dx (abar_k a_k / 2 + sum_{k' < k} abar_k' a_k')
 // (derivative of a_k = exp(-dx (m_k/2 + sum_{k'>k} m_k')) w.r.t. the mu
 // samples m of the ray).  One thread per ray.
@@ -307,7 +385,7 @@ extern "C" int boac_score_grad(const boac_geom* g, const boac_tissue* t, const f
     if (F_out) cudaMemcpyAsync(F_out, Fk, sizeof(float) * cnt_pix, cudaMemcpyDeviceToDevice, st);
     qbar_final_kernel<<<g1b, 256, 0, st>>>(B, (int)vb, S, s_stride, qK, qbar);
     backproject_table(g, B, tab, qbar, dx, Fbar, 0, partial, st);
-    abar_accum_kernel<<<rg, kRayThreads, 0, st>>>(n, V, dx, qbar, Fk, nullptr, nullptr, abar);
+    abar_accum(g, B, dx, qbar, Fk, nullptr, nullptr, abar, st);
 
     // ---- reverse through the iterations, one checkpoint segment at a time
     const int nseg = (K + ckpt_every - 1) / ckpt_every;
@@ -328,14 +406,14 @@ extern "C" int boac_score_grad(const boac_geom* g, const boac_tissue* t, const f
             project_table(g, B, tab, zbar, dx, rbar, st);
             qbar_step_kernel<<<g1b, 256, 0, st>>>(B, (int)vb, S, s_stride, q, rbar, qbar);
             backproject_table(g, B, tab, qbar, dx, Fnew, 1, partial, st);
-            abar_accum_kernel<<<rg, kRayThreads, 0, st>>>(n, V, dx, r, zbar, qbar, Fn, abar);
+            abar_accum(g, B, dx, r, zbar, qbar, Fn, abar, st);
             float* tmp = Fbar;
             Fbar = Fnew;
             Fnew = tmp;
         }
     }
     // sens = A^T 1
-    abar_accum_kernel<<<rg, kRayThreads, 0, st>>>(n, V, dx, nullptr, sensbar, nullptr, nullptr, abar);
+    abar_accum(g, B, dx, nullptr, sensbar, nullptr, nullptr, abar, st);
     // attenuation -> mu samples -> pixels -> coefficients
     mbar_kernel<<<rg, kRayThreads, 0, st>>>(n, V, dx, tab, abar);
     backproject_table(g, B, abar, nullptr, 1.0f, mubar, 0, partial, st);
