@@ -88,8 +88,9 @@ struct BandShape {
     static constexpr int SC = (LC + TC - 1) / TC; // column-run steps per thread
     static constexpr int SR = (LC + 1) / 2;       // row-run steps per thread (bound)
     static constexpr int REC = 8 + 4 * N;         // ints per (band, grid) record
-    // table floats per grid: Xc (column-run order), XrT (row-run order), Uc, Ur
-    static constexpr size_t GSTRIDE = (size_t)(SC + SR) * NT + 2 * N;
+    // table floats per grid: Xc and XrC (column-run order), XrT (row-run
+    // order), Uc, Ur
+    static constexpr size_t GSTRIDE = (size_t)(2 * SC + SR) * NT + 2 * N;
     static_assert(band_start<NB>(NB - 1) < N && band_start<NB>(NB) == N, "every band owns a row");
     static_assert(TC * N == NT && 4 * N == NT, "thread mapping");
 };
@@ -410,7 +411,8 @@ __global__ void __launch_bounds__(1024, 1) mlem_band_kernel(FusedArgs a) {
             const int* colLo = recs + rb * S::REC + kRecHdr;
             const int* colLen = colLo + N;
             float* Xc = tab + gi * S::GSTRIDE;
-            float* XrT = Xc + S::SC * NT;
+            float* XrC = Xc + S::SC * NT;
+            float* XrT = XrC + S::SC * NT;
             float* Uc = XrT + S::SR * NT;
             float* Ur = Uc + N;
             float* pb_ = pub + buf * 4 * N;
@@ -479,8 +481,13 @@ __global__ void __launch_bounds__(1024, 1) mlem_band_kernel(FusedArgs a) {
                 float pre = before;
                 for (int s = 0; s < x.rcnt; ++s) {
                     const int b = x.rlo + x.rb0 + s;
-                    const float m = W[(x.rk - colLo[b]) * WP + b];
-                    XrT[s * NT + tid] = ndl * (0.5f * m + pre);
+                    const int j = x.rk - colLo[b];
+                    const float m = W[j * WP + b];
+                    const float y = ndl * (0.5f * m + pre);
+                    XrT[s * NT + tid] = y;
+                    // the same exponent at the sample's place in the column runs
+                    const int cS = (colLen[b] + TC - 1) / TC, q3 = j / cS;
+                    XrC[(j - q3 * cS) * NT + q3 * N + b] = y;
                     pre += m;
                 }
                 if (rq == 0) Ur[x.rk] = ndl * total;
@@ -566,7 +573,8 @@ __global__ void __launch_bounds__(1024, 1) mlem_band_kernel(FusedArgs a) {
                 const int* colLo = recs + rb * S::REC + kRecHdr;
                 const int* colLen = colLo + N;
                 const float* Xc = tab + gi * S::GSTRIDE;
-                const float* XrT = Xc + S::SC * NT;
+                const float* XrC = Xc + S::SC * NT;
+                const float* XrT = XrC + S::SC * NT;
                 const float* Uc = XrT + S::SR * NT;
                 const float* Ur = Uc + N;
                 float* pb_ = pub + buf * 4 * N;
@@ -576,8 +584,11 @@ __global__ void __launch_bounds__(1024, 1) mlem_band_kernel(FusedArgs a) {
                     const float* nxt = tab + gn * S::GSTRIDE;
                     const int* rn = geo + (size_t)gn * S::REC;
                     const int lc = (__ldg(rn + kRecSc) * NT) / 32, lr = (__ldg(rn + kRecSr) * NT) / 32;
-                    for (int l = tid; l < lc; l += NT) prefetch_l2(nxt + 32 * l);
-                    for (int l = tid; l < lr; l += NT) prefetch_l2(nxt + S::SC * NT + 32 * l);
+                    for (int l = tid; l < lc; l += NT) {
+                        prefetch_l2(nxt + 32 * l);
+                        prefetch_l2(nxt + S::SC * NT + 32 * l);
+                    }
+                    for (int l = tid; l < lr; l += NT) prefetch_l2(nxt + 2 * S::SC * NT + 32 * l);
                 }
                 const int v1 = band_base_view(gi, V), v2 = (v1 + V / 2) % V;
                 const int v3 = (v1 + V / 4) % V, v4 = (v1 + 3 * V / 4) % V;
@@ -657,22 +668,17 @@ __global__ void __launch_bounds__(1024, 1) mlem_band_kernel(FusedArgs a) {
                 rb ^= 1;
                 __syncthreads();
                 if (scoring) continue;
-                {   // back-projection weights, column views
+                {   // back-projection weights G = dx sum_v a_v r_v of the grid's
+                    // four views in one pass over the column runs (the row
+                    // views' exponents in column-run order: XrC)
                     const float uc = Uc[cb];
                     const float r1 = rr[cb], r2 = rr[N + cb];
                     for (int s = 0; s < x.ccnt; ++s) {
+                        const int k = x.clo + x.ck0 + s;
                         const float y = Xc[s * NT + tid];
-                        W[(x.ck0 + s) * WP + cb] = fmaf(ex2(y), r1, ex2(uc - y) * r2);
-                    }
-                }
-                __syncthreads();
-                if (x.rcnt > 0) {  // row views
-                    const float ur = Ur[x.rk];
-                    const float r3 = rr[2 * N + x.rk], r4 = rr[3 * N + x.rk];
-                    for (int s = 0; s < x.rcnt; ++s) {
-                        const int b = x.rlo + x.rb0 + s;
-                        const float y = XrT[s * NT + tid];
-                        W[(x.rk - colLo[b]) * WP + b] += fmaf(ex2(y), r3, ex2(ur - y) * r4);
+                        const float z = XrC[s * NT + tid];
+                        const float gc = fmaf(ex2(y), r1, ex2(uc - y) * r2);
+                        W[(x.ck0 + s) * WP + cb] = gc + fmaf(ex2(z), rr[2 * N + k], ex2(Ur[k] - z) * rr[3 * N + k]);
                     }
                 }
                 __syncthreads();
