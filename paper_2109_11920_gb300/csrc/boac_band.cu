@@ -97,10 +97,36 @@ struct BandShape {
 
 // Record layout per (band, grid): [0] first active row kmin, [1] active rows
 // R, [2] threads per row T, [3] column steps, [4] row steps, [5], [6] the
-// base view's cos and sin (float bits), [7] unused,
+// base view's cos and sin (float bits), [7] the 5-class scatter lattice
+// (beta, 0: none, see band_scatter5),
 // then col_lo[n], col_len[n] (the run of column b: k in [lo, lo + len)),
 // row_lo[n], row_len[n] (the run of row k: b in [lo, lo + len)).
-enum { kRecKmin = 0, kRecRows = 1, kRecT = 2, kRecSc = 3, kRecSr = 4, kRecCos = 5, kRecSin = 6, kRecHdr = 8 };
+enum { kRecKmin = 0, kRecRows = 1, kRecT = 2, kRecSc = 3, kRecSr = 4, kRecCos = 5, kRecSin = 6, kRecLat = 7,
+       kRecHdr = 8 };
+
+// Five-class alternative to the 9-class scatter: class cls holds the
+// samples with k + beta b = cls (mod 5), beta in {2, 3}.  Two samples of one
+// class differ by a lattice vector (m, n) with m + beta n = 0 (mod 5); their
+// footprints are disjoint if the rotated vector (n cs - m sn, n sn + m cs) is
+// at least 2 pixels long along an image axis.  Vectors with |m| or |n| > 2
+// are at least 3 long (so more than 2 along some axis); those inside the box
+// |m|, |n| <= 2 are tested, with a margin for the rounding of the sample
+// coordinates.  Returns beta, or 0 where neither lattice qualifies (within
+// about 0.05 degrees of the axes).
+__host__ __device__ inline int scatter5_beta(float cs, float sn) {
+    for (int beta = 3; beta >= 2; --beta) {
+        bool good = true;
+        for (int m = -2; m <= 2; ++m)
+            for (int n = -2; n <= 2; ++n) {
+                if ((m == 0 && n == 0) || (m + beta * n + 25) % 5 != 0) continue;
+                const float du = fabsf((float)n * cs - (float)m * sn);
+                const float dw = fabsf((float)n * sn + (float)m * cs);
+                if (fmaxf(du, dw) < 2.001f) good = false;
+            }
+        if (good) return beta;
+    }
+    return 0;
+}
 
 // Base view of grid gi (views gi + j V/4): gi itself when its angle is at
 // most 45 degrees, else gi - V/4 (= gi + 3V/4), whose angle is in (-45, 0).
@@ -217,6 +243,7 @@ __global__ void __launch_bounds__(256) band_records_kernel(int V, int* geo, int*
         rec[kRecSr] = s_sr;
         rec[kRecCos] = __float_as_int(cs);
         rec[kRecSin] = __float_as_int(sn);
+        rec[kRecLat] = scatter5_beta(cs, sn);
         if (s_bad || s_sc > S::SC || s_sr > S::SR) atomicExch(bad, 1);
     }
 }
@@ -242,6 +269,29 @@ struct BandSmem {
     static_assert(S::REC % 4 == 0, "records are copied in 16-byte pieces");
     static_assert(BYTES <= 227 * 1024, "shared memory of one CTA");
 };
+
+// The 5-class scatter (beta from the grid's record): 4 threads per column
+// walk the column run's samples of each class.  Ends with a barrier.
+template <int NB>
+__device__ __forceinline__ void band_scatter5(const float* W, float* Ab, const int* colLo, const int* colLen,
+                                              int R0, float cs, float sn, float c, int beta) {
+    using S = BandShape<NB>;
+    constexpr int N = S::N, NT = S::NT, WP = S::WP, P = S::P, M = NT / N;
+    const int tid = threadIdx.x, b = tid % N, mm = tid / N;
+    const int lo = colLo[b], len = colLen[b];
+#pragma unroll
+    for (int cls = 0; cls < 5; ++cls) {
+        const int r5 = (cls + (5 - beta) * b) % 5;  // the class's k (mod 5) in column b
+        const int k1 = lo + (r5 - lo % 5 + 5) % 5;
+        for (int k = k1 + 5 * mm; k < lo + len; k += 5 * M) {
+            const float g = W[(k - lo) * WP + b];
+            float u, w;
+            sample_uw(k, b, cs, sn, c, &u, &w);
+            scatter_band<P>(Ab, R0, u, w, g);
+        }
+        __syncthreads();
+    }
+}
 
 // The 9-class race-free scatter of the sample buffer into the accumulator
 // band (two samples of one class are >= 3 lattice steps apart, so their 2x2
@@ -513,7 +563,10 @@ __global__ void __launch_bounds__(1024, 1) mlem_band_kernel(FusedArgs a) {
                 }
             }
             __syncthreads();
-            band_scatter<NB>(W, Ab, colLo, colLen, R0, cs, sn, c);
+            if (const int beta = colLo[kRecLat - kRecHdr])  // this grid's record
+                band_scatter5<NB>(W, Ab, colLo, colLen, R0, cs, sn, c, beta);
+            else
+                band_scatter<NB>(W, Ab, colLo, colLen, R0, cs, sn, c);
         }
         cl.sync();  // every band's accumulator complete
         for (int i = tid; i < rows * N; i += NT) {
@@ -682,7 +735,10 @@ __global__ void __launch_bounds__(1024, 1) mlem_band_kernel(FusedArgs a) {
                     }
                 }
                 __syncthreads();
-                band_scatter<NB>(W, Ab, colLo, colLen, R0, cs, sn, c);
+                if (const int beta = colLo[kRecLat - kRecHdr])  // this grid's record
+                    band_scatter5<NB>(W, Ab, colLo, colLen, R0, cs, sn, c, beta);
+                else
+                    band_scatter<NB>(W, Ab, colLo, colLen, R0, cs, sn, c);
             }
             if (scoring) break;
             // multiplicative update of the band's rows; the first row also
