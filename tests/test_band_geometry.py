@@ -97,3 +97,61 @@ def test_band_heights_fill_the_image():
     for nb in (5, 6, 8):
         st = band_starts(nb)
         assert st[0] == 0 and st[-1] == N and all(b > a for a, b in zip(st, st[1:]))
+
+
+def scatter5_beta(cs, sn):
+    """The kernel's choice of 5-class lattice {k + beta b = c (mod 5)} (0: none)."""
+    for beta in (3, 2):
+        good = True
+        for m in range(-2, 3):
+            for n in range(-2, 3):
+                if (m == 0 and n == 0) or (m + beta * n + 25) % 5:
+                    continue
+                du = abs(F32(n) * cs - F32(m) * sn)
+                dw = abs(F32(n) * sn + F32(m) * cs)
+                if max(du, dw) < 2.001:
+                    good = False
+        if good:
+            return beta
+    return 0
+
+
+def footprints_disjoint(u, w, inside, cls):
+    """No pixel is touched by two samples of one class (bilinear 2x2 footprints)."""
+    fj = np.floor(u).astype(np.int64)
+    fi = np.floor(w).astype(np.int64)
+    for c in np.unique(cls[inside]):
+        sel = inside & (cls == c)
+        pix = np.concatenate([((fi[sel] + di) * (N + 2) + fj[sel] + dj) for di in (0, 1) for dj in (0, 1)])
+        if len(np.unique(pix)) != len(pix):
+            return False
+    return True
+
+
+@pytest.mark.parametrize("V", [16, 120, 180])
+def test_scatter_classes_are_race_free(V):
+    """Brute force over every grid: the 9-class split (k mod 3, b mod 3) and,
+    where the kernel picks one, the 5-class lattice give disjoint footprints
+    within each class; the 5-class choice exists away from the axes."""
+    K, B = np.meshgrid(np.arange(N), np.arange(N), indexing="ij")
+    for gi in range(V // 4):
+        base = gi if 8 * gi <= V else gi + 3 * V // 4
+        cs, sn = cos_sin(base % V, V)
+        u, w = sample_uw(cs, sn)
+        inside = (u > -1) & (u < N) & (w > -1) & (w < N)
+        assert footprints_disjoint(u, w, inside, (K % 3) * 3 + (B % 3))
+        beta = scatter5_beta(cs, sn)
+        if abs(float(sn)) > 1e-3:
+            assert beta in (2, 3)
+        if beta:
+            assert footprints_disjoint(u, w, inside, (K + beta * B) % 5)
+
+
+def test_a_bad_lattice_is_caught():
+    """The brute-force check is not vacuous: 4 classes (k mod 2, b mod 2) let
+    footprints overlap at 30 degrees."""
+    cs, sn = F32(math.cos(math.radians(30))), F32(math.sin(math.radians(30)))
+    K, B = np.meshgrid(np.arange(N), np.arange(N), indexing="ij")
+    u, w = sample_uw(cs, sn)
+    inside = (u > -1) & (u < N) & (w > -1) & (w < N)
+    assert not footprints_disjoint(u, w, inside, (K % 2) * 2 + (B % 2))
