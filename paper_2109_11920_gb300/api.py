@@ -216,16 +216,17 @@ class BoacScore(torch.autograd.Function):
 # ---------------------------------------------------------------- ragged
 # Launch configurations per size class: ids 0-5 are the one-CTA kernel's
 # shapes (2 * shape + 1 for two views per grid); ids 6-8 the cluster kernel
-# (5, 6 or 8 CTAs per candidate) for 256 x 256 images with V % 4 == 0.
+# for V % 4 == 0: 5, 6 or 8 CTAs per candidate for 256 x 256 images, 2, 4 or
+# 8 for 128 x 128.
 N_CONFIGS = 9
 N_SINGLE_CTA_CONFIGS = 6
-BAND_CLUSTER_SIZES = {6: 5, 7: 6, 8: 8}
+BAND_CLUSTER_SIZES = {256: {6: 5, 7: 6, 8: 8}, 128: {6: 2, 7: 4, 8: 8}}
 
 
 def config_valid(g, cfg: int) -> bool:
     """Whether launch configuration ``cfg`` applies to geometry ``g``."""
-    if cfg in BAND_CLUSTER_SIZES:
-        return g.n == 256 and g.n_views % 4 == 0
+    if cfg >= N_SINGLE_CTA_CONFIGS:
+        return cfg in BAND_CLUSTER_SIZES.get(g.n, {}) and g.n_views % 4 == 0
     if not 0 <= cfg < N_SINGLE_CTA_CONFIGS:
         return False
     return g.n_views % 2 == 0 and (cfg % 2 == 1 or g.n_views % 4 == 0)

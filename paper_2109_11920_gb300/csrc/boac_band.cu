@@ -56,25 +56,26 @@ namespace boac {
 // over the 180-view grids of the busiest band's samples by 5 % (sizes found
 // by a local search of that sum); the other cluster sizes gain nothing
 // within their shared-memory room and use equal heights.
-template <int NB>
+template <int N, int NB>
 __host__ __device__ constexpr int band_start(int r) {
-    if (NB == 5)
+    if (N == 256 && NB == 5)
         return r <= 0 ? 0 : r == 1 ? 52 : r == 2 ? 103 : r == 3 ? 152 : r == 4 ? 203 : 256;
-    return r * ((256 + NB - 1) / NB) < 256 ? r * ((256 + NB - 1) / NB) : 256;
+    return r * ((N + NB - 1) / NB) < N ? r * ((N + NB - 1) / NB) : N;
 }
 
-template <int NB>
+template <int N, int NB>
 __host__ __device__ constexpr int band_max_rows() {
     int h = 0;
-    for (int r = 0; r < NB; ++r) h = band_start<NB>(r + 1) - band_start<NB>(r) > h ? band_start<NB>(r + 1) - band_start<NB>(r) : h;
+    for (int r = 0; r < NB; ++r)
+        h = band_start<N, NB>(r + 1) - band_start<N, NB>(r) > h ? band_start<N, NB>(r + 1) - band_start<N, NB>(r) : h;
     return h;
 }
 
-template <int NB>
+template <int N_, int NB>
 struct BandShape {
-    static constexpr int N = 256;
-    static constexpr int NT = 1024;
-    static constexpr int H = band_max_rows<NB>();  // rows of the tallest band
+    static constexpr int N = N_;
+    static constexpr int NT = 4 * N_;
+    static constexpr int H = band_max_rows<N_, NB>();  // rows of the tallest band
     // Padded band image: pixel (i, j), j in [-1, n], at local row i - R0 + 1,
     // column j + 1; the right padding column of a row and the left padding
     // column of the next are the same zero cell.
@@ -91,7 +92,7 @@ struct BandShape {
     // table floats per grid: Xc and XrC (column-run order), XrT (row-run
     // order), Uc, Ur
     static constexpr size_t GSTRIDE = (size_t)(2 * SC + SR) * NT + 2 * N;
-    static_assert(band_start<NB>(NB - 1) < N && band_start<NB>(NB) == N, "every band owns a row");
+    static_assert(band_start<N_, NB>(NB - 1) < N && band_start<N_, NB>(NB) == N, "every band owns a row");
     static_assert(TC * N == NT && 4 * N == NT, "thread mapping");
 };
 
@@ -135,11 +136,11 @@ __host__ __device__ __forceinline__ int band_base_view(int gi, int V) {
 }
 
 // Band of a sample whose footprint's top row is fi (fi = -1: band 0).
-template <int NB>
+template <int N, int NB>
 __device__ __forceinline__ int band_of_row(int fi) {
     int r = 0;
 #pragma unroll
-    for (int q = 1; q < NB; ++q) r += fi >= band_start<NB>(q);
+    for (int q = 1; q < NB; ++q) r += fi >= band_start<N, NB>(q);
     return r;
 }
 
@@ -175,10 +176,9 @@ __device__ __forceinline__ void scatter_band(float* img, int R0, float u, float 
 // by testing every k; thread k then finds the run of row k from the column
 // runs.  A run that is not contiguous or exceeds the main kernel's buffers
 // sets *bad (the main kernel then does nothing).
-template <int NB>
-__global__ void __launch_bounds__(256) band_records_kernel(int V, int* geo, int* bad) {
-    using S = BandShape<NB>;
-    constexpr int N = S::N;
+template <int N, int NB>
+__global__ void __launch_bounds__(N) band_records_kernel(int V, int* geo, int* bad) {
+    using S = BandShape<N, NB>;
     const int gi = blockIdx.x, r = blockIdx.y, ngrid = V / 4, t = threadIdx.x;
     int* rec = geo + ((size_t)r * ngrid + gi) * S::REC;
     __shared__ int s_lo[N], s_len[N];
@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(256) band_records_kernel(int V, int* geo, int*
     for (int k = 0; k < N; ++k) {
         float u, w;
         sample_uw(k, t, cs, sn, c, &u, &w);
-        if (inside_open(u, w, N) && band_of_row<NB>((int)floorf(w)) == r) {
+        if (inside_open(u, w, N) && band_of_row<N, NB>((int)floorf(w)) == r) {
             if (lo < 0) lo = k;
             hi = k;
             ++cnt;
@@ -252,9 +252,9 @@ __global__ void __launch_bounds__(256) band_records_kernel(int V, int* geo, int*
 // Shared-memory layout (bytes): 32 doubles for the score reduction, 16 ints
 // of flags, then floats, then two slots holding a grid's record (copied
 // from global memory with cp.async).
-template <int NB>
+template <int N, int NB>
 struct BandSmem {
-    using S = BandShape<NB>;
+    using S = BandShape<N, NB>;
     static constexpr int F0 = 0;                        // F band (mu during set-up)
     static constexpr int A0 = F0 + S::BIMG;             // accumulator band
     static constexpr int W0 = A0 + S::BIMG;             // [LC][WP] sample buffer
@@ -272,11 +272,11 @@ struct BandSmem {
 
 // The 5-class scatter (beta from the grid's record): 4 threads per column
 // walk the column run's samples of each class.  Ends with a barrier.
-template <int NB>
+template <int N, int NB>
 __device__ __forceinline__ void band_scatter5(const float* W, float* Ab, const int* colLo, const int* colLen,
                                               int R0, float cs, float sn, float c, int beta) {
-    using S = BandShape<NB>;
-    constexpr int N = S::N, NT = S::NT, WP = S::WP, P = S::P, M = NT / N;
+    using S = BandShape<N, NB>;
+    constexpr int NT = S::NT, WP = S::WP, P = S::P, M = NT / N;
     const int tid = threadIdx.x, b = tid % N, mm = tid / N;
     const int lo = colLo[b], len = colLen[b];
 #pragma unroll
@@ -297,11 +297,11 @@ __device__ __forceinline__ void band_scatter5(const float* W, float* Ab, const i
 // band (two samples of one class are >= 3 lattice steps apart, so their 2x2
 // footprints are disjoint); columns b = pb (mod 3) get NT / #columns threads
 // each, which walk the run's samples k = pk (mod 3).  Ends with a barrier.
-template <int NB>
+template <int N, int NB>
 __device__ __forceinline__ void band_scatter(const float* W, float* Ab, const int* colLo, const int* colLen,
                                              int R0, float cs, float sn, float c) {
-    using S = BandShape<NB>;
-    constexpr int N = S::N, NT = S::NT, WP = S::WP, P = S::P;
+    using S = BandShape<N, NB>;
+    constexpr int NT = S::NT, WP = S::WP, P = S::P;
     const int tid = threadIdx.x;
 #pragma unroll  // constant class offsets and column counts: +16 % measured
     for (int cls = 0; cls < 9; ++cls) {
@@ -323,19 +323,19 @@ __device__ __forceinline__ void band_scatter(const float* W, float* Ab, const in
     }
 }
 
-template <int NB>
-__global__ void __launch_bounds__(1024, 1) mlem_band_kernel(FusedArgs a) {
-    using S = BandShape<NB>;
-    using L = BandSmem<NB>;
-    constexpr int N = S::N, NT = S::NT, H = S::H, P = S::P, BIMG = S::BIMG, WP = S::WP, TC = S::TC;
+template <int N, int NB>
+__global__ void __launch_bounds__(4 * N, (N == 128 && NB > 2) ? 2 : 1) mlem_band_kernel(FusedArgs a) {
+    using S = BandShape<N, NB>;
+    using L = BandSmem<N, NB>;
+    constexpr int NT = S::NT, H = S::H, P = S::P, BIMG = S::BIMG, WP = S::WP, TC = S::TC;
     constexpr float kLog2e = 1.44269504088896340736f;
     if (*a.geo_bad) return;  // set before this launch: uniform over all CTAs
 
     cg::cluster_group cl = cg::this_cluster();
     const int r = (int)cl.block_rank();
     const int hold = blockIdx.x / NB;
-    const int R0 = band_start<NB>(r);
-    const int rows = band_start<NB>(r + 1) - R0;
+    const int R0 = band_start<N, NB>(r);
+    const int rows = band_start<N, NB>(r + 1) - R0;
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double* dred = reinterpret_cast<double*>(smem_raw);
@@ -564,15 +564,15 @@ __global__ void __launch_bounds__(1024, 1) mlem_band_kernel(FusedArgs a) {
             }
             __syncthreads();
             if (const int beta = colLo[kRecLat - kRecHdr])  // this grid's record
-                band_scatter5<NB>(W, Ab, colLo, colLen, R0, cs, sn, c, beta);
+                band_scatter5<N, NB>(W, Ab, colLo, colLen, R0, cs, sn, c, beta);
             else
-                band_scatter<NB>(W, Ab, colLo, colLen, R0, cs, sn, c);
+                band_scatter<N, NB>(W, Ab, colLo, colLen, R0, cs, sn, c);
         }
         cl.sync();  // every band's accumulator complete
         for (int i = tid; i < rows * N; i += NT) {
             const int l = i / N + 1, j = i % N;
             float v = Ab[l * P + j + 1];
-            if (l == 1 && r > 0) v += remote(Ab, r - 1)[(R0 - band_start<NB>(r - 1) + 1) * P + j + 1];
+            if (l == 1 && r > 0) v += remote(Ab, r - 1)[(R0 - band_start<N, NB>(r - 1) + 1) * P + j + 1];
             sens[i] = v;
         }
         // second part of a cut candidate: rank 0 waits for the first part,
@@ -736,9 +736,9 @@ __global__ void __launch_bounds__(1024, 1) mlem_band_kernel(FusedArgs a) {
                 }
                 __syncthreads();
                 if (const int beta = colLo[kRecLat - kRecHdr])  // this grid's record
-                    band_scatter5<NB>(W, Ab, colLo, colLen, R0, cs, sn, c, beta);
+                    band_scatter5<N, NB>(W, Ab, colLo, colLen, R0, cs, sn, c, beta);
                 else
-                    band_scatter<NB>(W, Ab, colLo, colLen, R0, cs, sn, c);
+                    band_scatter<N, NB>(W, Ab, colLo, colLen, R0, cs, sn, c);
             }
             if (scoring) break;
             // multiplicative update of the band's rows; the first row also
@@ -747,7 +747,7 @@ __global__ void __launch_bounds__(1024, 1) mlem_band_kernel(FusedArgs a) {
             for (int i = tid; i < rows * N; i += NT) {
                 const int l = i / N + 1, j = i % N, pi = l * P + j + 1;
                 float acc = Ab[pi];
-                if (l == 1 && r > 0) acc += remote(Ab, r - 1)[(R0 - band_start<NB>(r - 1) + 1) * P + j + 1];
+                if (l == 1 && r > 0) acc += remote(Ab, r - 1)[(R0 - band_start<N, NB>(r - 1) + 1) * P + j + 1];
                 const float sv = sens[i];
                 Fb[pi] = sv > 0.0f ? Fb[pi] * acc / sv : 0.0f;
             }
@@ -780,69 +780,58 @@ __global__ void __launch_bounds__(1024, 1) mlem_band_kernel(FusedArgs a) {
 }
 
 // ---------------------------------------------------------------- host side
-template <int NB>
-static const void* band_kernel_ptr() {
-    return reinterpret_cast<const void*>(mlem_band_kernel<NB>);
-}
-
-static bool band_nb_ok(int nb) { return nb == 5 || nb == 6 || nb == 8; }
+// Instantiated (image side, cluster size) pairs.
+#define BOAC_BAND_CASES(X) X(256, 5) X(256, 6) X(256, 8) X(128, 2) X(128, 4) X(128, 8)
 
 bool band_supported(int n, int V, int nb) {
-    return n == 256 && V % 4 == 0 && V >= 4 && V <= kMaxViews && band_nb_ok(nb);
+    if (V % 4 != 0 || V < 4 || V > kMaxViews) return false;
+#define X(NV, BV) if (n == NV && nb == BV) return true;
+    BOAC_BAND_CASES(X)
+#undef X
+    return false;
 }
 
-size_t band_smem_bytes(int nb) {
-    switch (nb) {
-        case 5: return BandSmem<5>::BYTES;
-        case 6: return BandSmem<6>::BYTES;
-        case 8: return BandSmem<8>::BYTES;
-        default: return 0;
-    }
+size_t band_smem_bytes(int n, int nb) {
+#define X(NV, BV) if (n == NV && nb == BV) return BandSmem<NV, BV>::BYTES;
+    BOAC_BAND_CASES(X)
+#undef X
+    return 0;
 }
 
-template <int NB>
-static size_t tab_floats_t(int V) {
-    return (size_t)(V / 4) * BandShape<NB>::GSTRIDE;
+size_t band_tab_floats(int n, int nb, int V) {
+#define X(NV, BV) if (n == NV && nb == BV) return (size_t)(V / 4) * BandShape<NV, BV>::GSTRIDE;
+    BOAC_BAND_CASES(X)
+#undef X
+    return 0;
 }
 
-size_t band_tab_floats(int nb, int V) {
-    switch (nb) {
-        case 5: return tab_floats_t<5>(V);
-        case 6: return tab_floats_t<6>(V);
-        case 8: return tab_floats_t<8>(V);
-        default: return 0;
-    }
+size_t band_sens_floats(int n, int nb) {
+#define X(NV, BV) if (n == NV && nb == BV) return (size_t)BandShape<NV, BV>::H * NV;
+    BOAC_BAND_CASES(X)
+#undef X
+    return 0;
 }
 
-size_t band_sens_floats(int nb) {
-    switch (nb) {
-        case 5: return (size_t)BandShape<5>::H * 256;
-        case 6: return (size_t)BandShape<6>::H * 256;
-        case 8: return (size_t)BandShape<8>::H * 256;
-        default: return 0;
-    }
+size_t band_geo_bytes(int n, int nb, int V) {
+    return sizeof(int) * (size_t)nb * (V / 4) * (8 + 4 * (size_t)n);
 }
 
-size_t band_geo_bytes(int nb, int V) {
-    return sizeof(int) * (size_t)nb * (V / 4) * (8 + 4 * 256);
-}
-
-template <int NB>
+template <int N, int NB>
 static int set_smem_attr() {
     constexpr int kDev = 64;
     static bool done[kDev];
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kDev) return launch_status();
     if (!done[dev]) {
-        if (cudaFuncSetAttribute(mlem_band_kernel<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)BandSmem<NB>::BYTES) != cudaSuccess)
+        if (cudaFuncSetAttribute(mlem_band_kernel<N, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)BandSmem<N, NB>::BYTES) != cudaSuccess)
             return launch_status();
         done[dev] = true;
     }
     return BOAC_OK;
 }
 
-template <int NB>
+template <int N, int NB>
 static int max_clusters_t() {
     constexpr int kDev = 64;
     static int cached[kDev];
@@ -852,7 +841,7 @@ static int max_clusters_t() {
         return 0;
     }
     if (cached[dev]) return cached[dev];
-    if (set_smem_attr<NB>() != BOAC_OK) return 0;
+    if (set_smem_attr<N, NB>() != BOAC_OK) return 0;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -860,12 +849,12 @@ static int max_clusters_t() {
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.gridDim = dim3(NB * 64, 1, 1);
-    cfg.blockDim = dim3(BandShape<NB>::NT, 1, 1);
-    cfg.dynamicSmemBytes = BandSmem<NB>::BYTES;
+    cfg.blockDim = dim3(BandShape<N, NB>::NT, 1, 1);
+    cfg.dynamicSmemBytes = BandSmem<N, NB>::BYTES;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, mlem_band_kernel<NB>, &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&n, mlem_band_kernel<N, NB>, &cfg) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -873,21 +862,19 @@ static int max_clusters_t() {
     return n;
 }
 
-int band_max_clusters(int nb) {
-    switch (nb) {
-        case 5: return max_clusters_t<5>();
-        case 6: return max_clusters_t<6>();
-        case 8: return max_clusters_t<8>();
-        default: return 0;
-    }
+int band_max_clusters(int n, int nb) {
+#define X(NV, BV) if (n == NV && nb == BV) return max_clusters_t<NV, BV>();
+    BOAC_BAND_CASES(X)
+#undef X
+    return 0;
 }
 
-template <int NB>
+template <int N, int NB>
 static int band_launch_t(const FusedArgs& a, int clusters, cudaStream_t st) {
-    int s = set_smem_attr<NB>();
+    int s = set_smem_attr<N, NB>();
     if (s != BOAC_OK) return s;
     if (cudaMemsetAsync(a.geo_bad, 0, sizeof(int), st) != cudaSuccess) return launch_status();
-    band_records_kernel<NB><<<dim3(a.V / 4, NB), 256, 0, st>>>(a.V, const_cast<int*>(a.geo), a.geo_bad);
+    band_records_kernel<N, NB><<<dim3(a.V / 4, NB), N, 0, st>>>(a.V, const_cast<int*>(a.geo), a.geo_bad);
     s = launch_status();
     if (s != BOAC_OK) return s;
     cudaLaunchConfig_t cfg = {};
@@ -897,23 +884,23 @@ static int band_launch_t(const FusedArgs& a, int clusters, cudaStream_t st) {
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.gridDim = dim3((unsigned)(clusters * NB), 1, 1);
-    cfg.blockDim = dim3(BandShape<NB>::NT, 1, 1);
-    cfg.dynamicSmemBytes = BandSmem<NB>::BYTES;
+    cfg.blockDim = dim3(BandShape<N, NB>::NT, 1, 1);
+    cfg.dynamicSmemBytes = BandSmem<N, NB>::BYTES;
     cfg.stream = st;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (cudaLaunchKernelEx(&cfg, mlem_band_kernel<NB>, a) != cudaSuccess) return launch_status();
+    if (cudaLaunchKernelEx(&cfg, mlem_band_kernel<N, NB>, a) != cudaSuccess) return launch_status();
     return launch_status();
 }
 
-int band_launch(int nb, const FusedArgs& a, int clusters, cudaStream_t st) {
+int band_launch(int n, int nb, const FusedArgs& a, int clusters, cudaStream_t st) {
     if (clusters < 1) return BOAC_EINVAL;
-    switch (nb) {
-        case 5: return band_launch_t<5>(a, clusters, st);
-        case 6: return band_launch_t<6>(a, clusters, st);
-        case 8: return band_launch_t<8>(a, clusters, st);
-        default: return BOAC_EUNSUPPORTED;
-    }
+#define X(NV, BV) if (n == NV && nb == BV) return band_launch_t<NV, BV>(a, clusters, st);
+    BOAC_BAND_CASES(X)
+#undef X
+    return BOAC_EUNSUPPORTED;
 }
+
+#undef BOAC_BAND_CASES
 
 }  // namespace boac

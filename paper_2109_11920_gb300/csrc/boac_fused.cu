@@ -425,9 +425,9 @@ __global__ void __launch_bounds__(NT, (fused_min_blocks<N, NT>())) mlem_fused_ke
 // ---------------------------------------------------------------- host side
 // Launch shapes: for each image side, CTAs of 2n, 4n or 8n threads (at most
 // 1024), with four or two views per sample grid: configuration id =
-// 2 * shape + (1 for two views per grid).  For 256 x 256 images, ids 6, 7
-// and 8 are the cluster kernel (boac_band.cu) with 5, 6 or 8 CTAs per
-// candidate (four views per grid only).
+// 2 * shape + (1 for two views per grid).  Ids 6, 7 and 8 are the cluster
+// kernel (boac_band.cu, four views per grid only): 5, 6 or 8 CTAs per
+// candidate for 256 x 256 images, 2, 4 or 8 for 128 x 128.
 constexpr int kShapes = 3;
 constexpr int kBandConfigs = 3;
 constexpr int kConfigs = 2 * kShapes + kBandConfigs;
@@ -468,15 +468,15 @@ static FusedVariant make_variant() {
                         fused_launch_t<N, NT, QUAD>};
 }
 
-template <int NB>
-static size_t band_smem_of(int) { return band_smem_bytes(NB); }
-template <int NB>
+template <int N, int NB>
+static size_t band_smem_of(int) { return band_smem_bytes(N, NB); }
+template <int N, int NB>
 static int band_launch_of(const FusedArgs& a, int clusters, cudaStream_t st) {
-    return band_launch(NB, a, clusters, st);
+    return band_launch(N, NB, a, clusters, st);
 }
-template <int NB>
+template <int N, int NB>
 static FusedVariant make_band_variant() {
-    return FusedVariant{256, 1024, true, NB, band_smem_of<NB>, nullptr, band_launch_of<NB>};
+    return FusedVariant{N, 4 * N, true, NB, band_smem_of<N, NB>, nullptr, band_launch_of<N, NB>};
 }
 
 #define BOAC_SHAPES(NV)                                                                        \
@@ -489,9 +489,10 @@ static FusedVariant make_band_variant() {
 static const FusedVariant* variant_table(int n) {
     static const FusedVariant t64[kConfigs] = {BOAC_SHAPES(64), BOAC_NO_BAND};
     static const FusedVariant t96[kConfigs] = {BOAC_SHAPES(96), BOAC_NO_BAND};
-    static const FusedVariant t128[kConfigs] = {BOAC_SHAPES(128), BOAC_NO_BAND};
-    static const FusedVariant t256[kConfigs] = {BOAC_SHAPES(256), make_band_variant<5>(),
-                                                make_band_variant<6>(), make_band_variant<8>()};
+    static const FusedVariant t128[kConfigs] = {BOAC_SHAPES(128), make_band_variant<128, 2>(),
+                                                make_band_variant<128, 4>(), make_band_variant<128, 8>()};
+    static const FusedVariant t256[kConfigs] = {BOAC_SHAPES(256), make_band_variant<256, 5>(),
+                                                make_band_variant<256, 6>(), make_band_variant<256, 8>()};
     switch (n) {
         case 64: return t64;
         case 96: return t96;
@@ -509,16 +510,26 @@ static int single_cta_config(const boac_geom* g) {
     return 2 * shape + (g->n_views % 4 == 0 ? 0 : 1);
 }
 
-// Default configuration: 256 x 256 images with V % 4 == 0 take the cluster
-// kernel with the cluster size that keeps the most SMs busy (clusters are
-// placed within one GPC, so the resident count depends on the size); the
-// smaller cluster on a tie.
-static int default_config(const boac_geom* g) {
+// Default configuration for B candidates.  256 x 256 images with V % 4 == 0
+// take the cluster kernel with the cluster size that keeps the most SMs
+// busy (clusters are placed within one GPC, so the resident count depends
+// on the size); the smaller cluster on a tie.  128 x 128 images with
+// V % 4 == 0 take the cluster kernel while the batch is too small to occupy
+// the SMs one candidate per CTA: 8 CTAs per candidate for B <= S/4, 4 for
+// B <= 0.45 S (S = SM count; measured on GB300 at 120 views: 1.8x the
+// one-CTA kernel at B = 8, 1.36x at B = 32, +4 % at B = 64, slower from
+// B = 96 on, where every candidate has an SM of its own).
+static int default_config(const boac_geom* g, int B) {
+    if (g->n == 128 && g->n_views % 4 == 0 && B >= 1) {
+        const int sms = sm_count();
+        if (sms > 0 && 4 * B <= sms && band_max_clusters(128, 8) > 0) return 2 * kShapes + 2;
+        if (sms > 0 && 20 * B <= 9 * sms && band_max_clusters(128, 4) > 0) return 2 * kShapes + 1;
+    }
     if (g->n == 256 && g->n_views % 4 == 0) {
         static const int nbs[kBandConfigs] = {5, 6, 8};
         int best = -1, best_ctas = 0;
         for (int i = 0; i < kBandConfigs; ++i) {
-            const int ctas = band_max_clusters(nbs[i]) * nbs[i];
+            const int ctas = band_max_clusters(256, nbs[i]) * nbs[i];
             if (ctas > best_ctas) {
                 best = i;
                 best_ctas = ctas;
@@ -588,10 +599,10 @@ static FusedLayout fused_layout(const boac_geom* g, const FusedVariant* v, int h
     l.status = 0;
     l.tab = 256;
     if (v->nb > 1) {
-        l.sens = l.tab + align256(sizeof(float) * ctas * band_tab_floats(v->nb, g->n_views));
-        l.img = l.sens + align256(sizeof(float) * ctas * band_sens_floats(v->nb));
+        l.sens = l.tab + align256(sizeof(float) * ctas * band_tab_floats(g->n, v->nb, g->n_views));
+        l.img = l.sens + align256(sizeof(float) * ctas * band_sens_floats(g->n, v->nb));
         l.geo = l.img + 256;
-        l.ready = l.geo + align256(band_geo_bytes(v->nb, g->n_views));
+        l.ready = l.geo + align256(band_geo_bytes(g->n, v->nb, g->n_views));
     } else {
         l.sens = l.tab + align256(sizeof(float) * ctas * fused_tab_floats(g->n, g->n_views));
         l.img = l.sens + align256(sizeof(float) * ctas * g->n * g->n);
@@ -611,7 +622,7 @@ static FusedLayout fused_layout(const boac_geom* g, const FusedVariant* v, int h
 static int variant_holders(const boac_geom* g, const FusedVariant* v, int B) {
     long long h;
     if (v->nb > 1) {
-        h = band_max_clusters(v->nb);
+        h = band_max_clusters(g->n, v->nb);
     } else {
         const int per_sm = variant_occupancy(v, g->n_views);
         h = (long long)per_sm * sm_count();
@@ -621,7 +632,7 @@ static int variant_holders(const boac_geom* g, const FusedVariant* v, int B) {
 }
 
 size_t fused_workspace_bytes(const boac_geom* g, int B) {
-    const FusedVariant* v = get_variant(g, default_config(g));
+    const FusedVariant* v = get_variant(g, default_config(g, B));
     const int h = v ? variant_holders(g, v, B) : 0;
     return h > 0 ? fused_layout(g, v, h, B).total : 0;
 }
@@ -704,7 +715,7 @@ static int ragged_plan(const boac_geom* classes, int n_classes, const boac_ragge
     size_t off = 256;
     for (int c = 0; c < n_classes; ++c) {
         if (!variant_table(classes[c].n)) return BOAC_EUNSUPPORTED;
-        const int cfg = config ? config[c] : default_config(&classes[c]);
+        const int cfg = config ? config[c] : default_config(&classes[c], pl->cls_count[c]);
         pl->var[c] = get_variant(&classes[c], cfg);
         if (!pl->var[c]) return BOAC_EINVAL;
         const int cnt = pl->cls_count[c];
@@ -742,7 +753,7 @@ extern "C" int boac_mlem(const boac_geom* g, const float* mu, const float* S, lo
                          size_t ws_bytes, void* stream) {
     if (!geom_ok(g) || !mu || !S || !F || B < 1 || K < 0 || s_stride < 0) return BOAC_EINVAL;
     if (g->n_views % 2) return BOAC_EINVAL;
-    const FusedVariant* v = get_variant(g, default_config(g));
+    const FusedVariant* v = get_variant(g, default_config(g, B));
     if (!v) return BOAC_EUNSUPPORTED;
     const int slots = variant_holders(g, v, B);
     if (slots <= 0) return BOAC_ECUDA;

@@ -82,17 +82,18 @@ __device__ __forceinline__ double loglik_term(double s, double q, int include_lg
     return t;
 }
 
-// ---- cluster kernel (boac_band.cu): images of side 256, V % 4 == 0, a
-// cluster of nb CTAs per candidate, nb in {5, 6, 8}.
+// ---- cluster kernel (boac_band.cu): images of side n split into bands of
+// rows over a cluster of nb CTAs per candidate, V % 4 == 0; instantiated for
+// n = 256 with nb in {5, 6, 8} and n = 128 with nb in {2, 4, 8}.
 bool band_supported(int n, int V, int nb);
-size_t band_smem_bytes(int nb);
-size_t band_tab_floats(int nb, int V);   // attenuation exponents, per CTA
-size_t band_sens_floats(int nb);         // sensitivity rows, per CTA
-size_t band_geo_bytes(int nb, int V);    // per-band ray-run records
+size_t band_smem_bytes(int n, int nb);
+size_t band_tab_floats(int n, int nb, int V);  // attenuation exponents, per CTA
+size_t band_sens_floats(int n, int nb);        // sensitivity rows, per CTA
+size_t band_geo_bytes(int n, int nb, int V);   // per-band ray-run records
 // Largest number of clusters of nb CTAs resident at once (cached per device;
 // 0 if the device cannot run them).
-int band_max_clusters(int nb);
+int band_max_clusters(int n, int nb);
 // Launch the record kernel and the cluster kernel with `clusters` clusters.
-int band_launch(int nb, const FusedArgs& a, int clusters, cudaStream_t st);
+int band_launch(int n, int nb, const FusedArgs& a, int clusters, cudaStream_t st);
 
 }  // namespace boac

@@ -11,22 +11,22 @@ import math
 import numpy as np
 import pytest
 
-N, NT = 256, 1024
+N = 256
 F32 = np.float32
 
 
-def band_starts(nb):
-    if nb == 5:
+def band_starts(nb, n=N):
+    if n == 256 and nb == 5:
         return [0, 52, 103, 152, 203, 256]
-    h = -(-N // nb)
-    return [min(r * h, N) for r in range(nb + 1)]
+    h = -(-n // nb)
+    return [min(r * h, n) for r in range(nb + 1)]
 
 
-def shape(nb):
-    st = band_starts(nb)
+def shape(nb, n=N):
+    st = band_starts(nb, n)
     H = max(st[r + 1] - st[r] for r in range(nb))
     LC = ((H + 1) * 141422 + 99999) // 100000 + 2
-    TC = NT // N
+    TC = 4  # threads per column: the CTA has 4 n threads
     return H, LC, (LC + TC - 1) // TC, (LC + 1) // 2
 
 
@@ -43,9 +43,9 @@ def fma32(a, b, c):
     return (a.astype(np.float64) * np.float64(b) + c.astype(np.float64)).astype(F32)
 
 
-def sample_uw(cs, sn):
-    c = F32(0.5 * (N - 1))
-    K, B = np.meshgrid(np.arange(N), np.arange(N), indexing="ij")
+def sample_uw(cs, sn, n=N):
+    c = F32(0.5 * (n - 1))
+    K, B = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
     kc = (K.astype(F32) - c).astype(F32)
     bc = (B.astype(F32) - c).astype(F32)
     u = fma32(-kc, sn, fma32(bc, cs, np.full_like(bc, c)))
@@ -64,17 +64,18 @@ def runs(mask, axis):
     return lens
 
 
-@pytest.mark.parametrize("nb", [5, 6, 8])
-@pytest.mark.parametrize("V,grids", [(16, None), (180, None), (720, range(0, 180, 7))])
-def test_band_runs_fit_the_kernel_buffers(nb, V, grids):
-    st = band_starts(nb)
-    H, LC, SC, SR = shape(nb)
+@pytest.mark.parametrize("n,nb", [(256, 5), (256, 6), (256, 8), (128, 2), (128, 4), (128, 8)])
+@pytest.mark.parametrize("V,grids", [(16, None), (120, None), (180, None), (720, range(0, 180, 7))])
+def test_band_runs_fit_the_kernel_buffers(n, nb, V, grids):
+    NT = 4 * n
+    st = band_starts(nb, n)
+    H, LC, SC, SR = shape(nb, n)
     for gi in (grids if grids is not None else range(V // 4)):
         base = gi if 8 * gi <= V else gi + 3 * V // 4
         cs, sn = cos_sin(base % V, V)
         assert cs > 0.7  # base angle within (-45, 45] degrees
-        u, w = sample_uw(cs, sn)
-        inside = (u > -1) & (u < N) & (w > -1) & (w < N)
+        u, w = sample_uw(cs, sn, n)
+        inside = (u > -1) & (u < n) & (w > -1) & (w < n)
         fi = np.floor(w).astype(int)
         band = np.searchsorted(np.array(st[1:-1]), fi, side="right")
         total = 0
@@ -84,7 +85,7 @@ def test_band_runs_fit_the_kernel_buffers(nb, V, grids):
             col = runs(m, 0)  # along k for every b
             row = runs(m, 1)  # along b for every k
             assert col.max() <= LC
-            assert int(np.max(-(-col // (NT // N)))) <= SC
+            assert int(np.max(-(-col // 4))) <= SC
             active = np.nonzero(row)[0]
             if len(active):
                 R = active[-1] - active[0] + 1
@@ -94,9 +95,9 @@ def test_band_runs_fit_the_kernel_buffers(nb, V, grids):
 
 
 def test_band_heights_fill_the_image():
-    for nb in (5, 6, 8):
-        st = band_starts(nb)
-        assert st[0] == 0 and st[-1] == N and all(b > a for a, b in zip(st, st[1:]))
+    for n, nb in ((256, 5), (256, 6), (256, 8), (128, 2), (128, 4), (128, 8)):
+        st = band_starts(nb, n)
+        assert st[0] == 0 and st[-1] == n and all(b > a for a, b in zip(st, st[1:]))
 
 
 def scatter5_beta(cs, sn):

@@ -50,8 +50,11 @@ def test_noalloc_matches_workspace_entry_point(cuda):
         st = call_noalloc(lib, g, mu, S, F, K, L)
         assert st == _lib.BOAC_OK, _lib.status_string(st)
         torch.cuda.synchronize()
+        # boac_mlem may run these 20 candidates on clusters of CTAs (small
+        # batch), the no-alloc entry point one CTA per candidate: the same
+        # arithmetic summed in another order
         assert rel_l2(F.cpu().numpy(), F_ref.cpu().numpy()) < 1e-5, call
-        np.testing.assert_allclose(L.cpu().numpy(), L_ref.cpu().numpy(), rtol=1e-9)
+        np.testing.assert_allclose(L.cpu().numpy(), L_ref.cpu().numpy(), rtol=1e-6)
     # arguments are still checked on the host
     F = torch.ones(20, p.n, p.n, device=cuda)
     L = torch.empty(20, dtype=torch.float64, device=cuda)
