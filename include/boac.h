@@ -155,8 +155,10 @@ int boac_backproject(const boac_geom *g, const float *mu, const float *y,
  *   L        [B] float64 output, or NULL to skip the score
  * boac_mlem is the batched path: one persistent fused kernel runs every
  * iteration of every candidate on chip (n <= 128: one CTA per candidate;
- * n = 256 with n_views % 4 == 0: a thread-block cluster per candidate, the
- * image split into bands of rows over its CTAs).  boac_mlem_plain is the
+ * n = 256 with n_views % 4 == 0, and n = 128 with n_views % 4 == 0 when B
+ * is too small to give every SM a candidate: a thread-block cluster per
+ * candidate, the image split into bands of rows over its CTAs).  The choice
+ * depends on B, so query the workspace with the same B.  boac_mlem_plain is the
  * launch-per-step path: one candidate at a time, separate project / ratio /
  * backproject / update kernels per iteration (the comparison baseline).
  * Workspace: boac_workspace_bytes(g, B, BOAC_OP_MLEM / BOAC_OP_MLEM_PLAIN). */
@@ -179,11 +181,12 @@ int boac_mlem_plain(const boac_geom *g, const float *mu, const float *S,
  * first.  config[c] (host array, or NULL for defaults) picks class c's launch
  * shape: 2 * shape + pair, shape 0/1/2 = CTAs of 2n/4n/8n (<= 1024) threads,
  * pair = 1 for two views per sample grid instead of four (four needs
- * n_views % 4 == 0); for n = 256 with n_views % 4 == 0, configurations 6, 7
- * and 8 run each candidate on a thread-block cluster of 5, 6 or 8 CTAs that
- * split the image into bands of rows (the default there: the cluster size
- * that keeps the most SMs busy).  An id that does not apply to a class is
- * BOAC_EINVAL.  The autotuner of the Python package chooses them.
+ * n_views % 4 == 0); with n_views % 4 == 0, configurations 6, 7 and 8 run
+ * each candidate on a thread-block cluster of CTAs that split the image into
+ * bands of rows: 5, 6 or 8 CTAs for n = 256 (the default there: the cluster
+ * size that keeps the most SMs busy), 2, 4 or 8 for n = 128 (the default
+ * for classes with few candidates).  An id that does not apply to a class
+ * is BOAC_EINVAL.  The autotuner of the Python package chooses them.
  *   classes  [n_classes] geometries (host), 1 <= n_classes <= 8, sides
  *            64/96/128/256
  *   cands    [B] descriptors (host)
