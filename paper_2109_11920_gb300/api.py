@@ -217,10 +217,10 @@ class BoacScore(torch.autograd.Function):
 # Launch configurations per size class: ids 0-5 are the one-CTA kernel's
 # shapes (2 * shape + 1 for two views per grid); ids 6-8 the cluster kernel
 # for V % 4 == 0: 5, 6 or 8 CTAs per candidate for 256 x 256 images, 2, 4 or
-# 8 for 128 x 128.
+# 8 for 128 x 128 and 64 x 64.
 N_CONFIGS = 9
 N_SINGLE_CTA_CONFIGS = 6
-BAND_CLUSTER_SIZES = {256: {6: 5, 7: 6, 8: 8}, 128: {6: 2, 7: 4, 8: 8}}
+BAND_CLUSTER_SIZES = {256: {6: 5, 7: 6, 8: 8}, 128: {6: 2, 7: 4, 8: 8}, 64: {6: 2, 7: 4, 8: 8}}
 
 
 def config_valid(g, cfg: int) -> bool:

@@ -324,7 +324,7 @@ __device__ __forceinline__ void band_scatter(const float* W, float* Ab, const in
 }
 
 template <int N, int NB>
-__global__ void __launch_bounds__(4 * N, (N == 128 && NB > 2) ? 2 : 1) mlem_band_kernel(FusedArgs a) {
+__global__ void __launch_bounds__(4 * N, N == 64 ? 4 : (N == 128 && NB > 2) ? 2 : 1) mlem_band_kernel(FusedArgs a) {
     using S = BandShape<N, NB>;
     using L = BandSmem<N, NB>;
     constexpr int NT = S::NT, H = S::H, P = S::P, BIMG = S::BIMG, WP = S::WP, TC = S::TC;
@@ -781,7 +781,8 @@ __global__ void __launch_bounds__(4 * N, (N == 128 && NB > 2) ? 2 : 1) mlem_band
 
 // ---------------------------------------------------------------- host side
 // Instantiated (image side, cluster size) pairs.
-#define BOAC_BAND_CASES(X) X(256, 5) X(256, 6) X(256, 8) X(128, 2) X(128, 4) X(128, 8)
+#define BOAC_BAND_CASES(X) \
+    X(256, 5) X(256, 6) X(256, 8) X(128, 2) X(128, 4) X(128, 8) X(64, 2) X(64, 4) X(64, 8)
 
 bool band_supported(int n, int V, int nb) {
     if (V % 4 != 0 || V < 4 || V > kMaxViews) return false;

@@ -84,7 +84,7 @@ __device__ __forceinline__ double loglik_term(double s, double q, int include_lg
 
 // ---- cluster kernel (boac_band.cu): images of side n split into bands of
 // rows over a cluster of nb CTAs per candidate, V % 4 == 0; instantiated for
-// n = 256 with nb in {5, 6, 8} and n = 128 with nb in {2, 4, 8}.
+// n = 256 with nb in {5, 6, 8} and n = 128 and 64 with nb in {2, 4, 8}.
 bool band_supported(int n, int V, int nb);
 size_t band_smem_bytes(int n, int nb);
 size_t band_tab_floats(int n, int nb, int V);  // attenuation exponents, per CTA

@@ -64,7 +64,7 @@ def runs(mask, axis):
     return lens
 
 
-@pytest.mark.parametrize("n,nb", [(256, 5), (256, 6), (256, 8), (128, 2), (128, 4), (128, 8)])
+@pytest.mark.parametrize("n,nb", [(256, 5), (256, 6), (256, 8), (128, 2), (128, 4), (128, 8), (64, 2), (64, 4), (64, 8)])
 @pytest.mark.parametrize("V,grids", [(16, None), (120, None), (180, None), (720, range(0, 180, 7))])
 def test_band_runs_fit_the_kernel_buffers(n, nb, V, grids):
     NT = 4 * n
@@ -95,7 +95,7 @@ def test_band_runs_fit_the_kernel_buffers(n, nb, V, grids):
 
 
 def test_band_heights_fill_the_image():
-    for n, nb in ((256, 5), (256, 6), (256, 8), (128, 2), (128, 4), (128, 8)):
+    for n, nb in ((256, 5), (256, 6), (256, 8), (128, 2), (128, 4), (128, 8), (64, 2), (64, 4), (64, 8)):
         st = band_starts(nb, n)
         assert st[0] == 0 and st[-1] == n and all(b > a for a, b in zip(st, st[1:]))
 

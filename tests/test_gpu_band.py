@@ -115,23 +115,24 @@ def test_largest_view_count(cuda):
     assert abs(float(L[0]) - Lo[0]) < 1e-6 * abs(Lo[0])
 
 
-def test_cluster_kernel_128(cuda):
-    """128 x 128 images on clusters of 2, 4 or 8 CTAs (configs 6-8) against
-    the oracle and the one-CTA kernel (config 4)."""
-    p = make_problem(128, 0.2, 120, 1e6, B=3, seed=61)
+@pytest.mark.parametrize("n,dx,V,cfg1", [(128, 0.2, 120, 4), (64, 0.4, 60, 2)])
+def test_cluster_kernel_small_images(cuda, n, dx, V, cfg1):
+    """128 x 128 and 64 x 64 images on clusters of 2, 4 or 8 CTAs (configs
+    6-8) against the oracle and the one-CTA kernel."""
+    p = make_problem(n, dx, V, 1e6, B=3, seed=61)
     g = Geom.make(p.n, p.dx, p.V)
     K = 4
     out = {}
-    for cfg in (4, 6, 7, 8):
+    for cfg in (cfg1, 6, 7, 8):
         batch = ragged_one_class(p, g, K, cuda)
         L = boac.boac_mlem_ragged(batch, config=[cfg]).cpu().numpy()
         out[cfg] = (batch.F_pool.cpu().numpy().copy(), L)
     Fo, Lo, _ = oracle.mlem_batch(p.geom, p.mu, p.S, K)
-    F4, L4 = out[4]
+    F4, L4 = out[cfg1]
     for cfg in (6, 7, 8):
         F, L = out[cfg]
         assert rel_l2(F, F4) < 1e-5, cfg
         np.testing.assert_allclose(L, L4, rtol=1e-6, atol=0)
         for b in range(3):
-            assert rel_l2(F[b * 128 * 128:(b + 1) * 128 * 128], Fo[b].ravel()) < 1e-4, (cfg, b)
+            assert rel_l2(F[b * n * n:(b + 1) * n * n], Fo[b].ravel()) < 1e-4, (cfg, b)
             assert abs(L[b] - Lo[b]) < 1e-6 * abs(Lo[b]), (cfg, b)
