@@ -192,8 +192,11 @@ def test_mlem_batched_full_size_sampled(cuda):
 
 def test_work_split_status_and_odd_batches(cuda, probs):
     """The fused kernel splits a batch's iterations evenly over its CTAs and
-    may cut a candidate between two of them; batches of every size give the
-    same images as one-candidate calls, and the workspace status stays OK."""
+    may cut a candidate between two of them.  At one launch configuration,
+    batches of every size give the same images as a one-candidate call, bit
+    for bit; boac_mlem's default configuration depends on the batch size, and
+    across configurations the results agree to float rounding.  The
+    workspace status stays OK."""
     p = probs[SHAPES[0]]
     g = geom(p)
     mu1 = T(p.mu[:1], cuda)
@@ -206,8 +209,18 @@ def test_work_split_status_and_odd_batches(cuda, probs):
         F = torch.ones(B, p.n, p.n, device=cuda)
         F, L = boac.boac_mlem(g, mu, S, F, 7, ws=ws)
         assert boac.boac_workspace_status(ws) == boac._lib.BOAC_OK
-        torch.testing.assert_close(F, F1.expand(B, p.n, p.n), rtol=0, atol=0)
-        torch.testing.assert_close(L, L1.expand(B), rtol=0, atol=0)
+        assert rel_l2(F.cpu().numpy(), F1.expand(B, p.n, p.n).cpu().numpy()) < 1e-5, B
+        torch.testing.assert_close(L, L1.expand(B), rtol=1e-6, atol=0)
+    for cfg in (2, 4):  # CTAs of 4n and 8n threads
+        first = None
+        for B in (1, 5, 153, 457):
+            batch = boac.RaggedBatch([g], [0] * B, [7] * B, [mu1[0]] * B, [S] * B, device=cuda)
+            L = boac.boac_mlem_ragged(batch, config=[cfg])
+            F = batch.F_pool.view(B, p.n, p.n)
+            if first is None:
+                first = (F[0].clone(), L[0].clone())
+            torch.testing.assert_close(F, first[0].expand(B, p.n, p.n), rtol=0, atol=0)
+            torch.testing.assert_close(L, first[1].expand(B), rtol=0, atol=0)
 
 
 def test_mlem_invariants_on_gpu(cuda, probs):
