@@ -68,6 +68,8 @@ def _load():
             lib.orc_score.restype = Dv
             lib.orc_score_grad.argtypes = geo + [Dv, Dv, Dv, D, D, I, I, D, D]
             lib.orc_score_grad.restype = Dv
+            lib.orc_score_grad_params.argtypes = geo + [D, D, I, I, D, D]
+            lib.orc_score_grad_params.restype = Dv
             lib.orc_mlem_batch.argtypes = geo + [I, D, D, ctypes.c_longlong,
                                                  ctypes.POINTER(ctypes.c_int), D, D, I, I]
             lib.orc_mlem_batch.restype = I
@@ -185,6 +187,18 @@ def score_grad(g: Geometry, tissue, coef, S, K: int, include_lgamma: bool = True
     F = np.zeros((g.n, g.n))
     L = _load().orc_score_grad(*g.args, mu_b, mu_c, dR, _d(c), _d(S), int(K),
                                int(include_lgamma), _d(grad), _d(F))
+    return L, grad, F
+
+
+def score_grad_params(g: Geometry, params, S, K: int, include_lgamma: bool = True):
+    """(L, dL/dp[9], F^K) for p = (c_0..c_5, mu_b, mu_c, dR): the same pipeline
+    as score_grad with the tissue values as variables (dR < 0 taken as 0)."""
+    p = _arr(params, (9,))
+    S = _arr(S, (g.V, g.nb))
+    grad = np.zeros(9)
+    F = np.zeros((g.n, g.n))
+    L = _load().orc_score_grad_params(*g.args, _d(p), _d(S), int(K), int(include_lgamma),
+                                      _d(grad), _d(F))
     return L, grad, F
 
 

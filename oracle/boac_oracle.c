@@ -28,7 +28,9 @@
  *   Eq. 5   ln P = sum_i S_i ln q_i - q_i - ln S_i!  (0 ln q := 0 for S_i=0;
  *           -inf when q_i = 0 < S_i).
  *   grad    exact reverse-mode derivative of Eq. 5 after K MLEM iterations
- *           with respect to c_0..c_5 (AREA mode, F^0 = 1).
+ *           with respect to c_0..c_5 (AREA mode, F^0 = 1), and in the
+ *           9-parameter form with respect to mu_b, mu_c and dR too (the
+ *           paper keeps those fixed; this form lets them be optimised).
  *
  * Geometry (the paper gives none; this is the reading used on both sides):
  *   pixel (i,j), row i, column j, centre x=(j-c)dx, y=(i-c)dx, c=(n-1)/2;
@@ -379,7 +381,9 @@ double orc_score(int n, int nb, int V, double dx, double ds, const double *mu,
 
 /* ------------------------------------------------------------------ */
 /* Reverse-mode gradient of Eq. 5 after K MLEM iterations from F^0 = 1,   */
-/* with respect to the Legendre coefficients (AREA rasterisation).        */
+/* with respect to the attenuation map (AREA rasterisation), then to the  */
+/* Legendre coefficients and, for the 9-parameter form, to mu_b, mu_c and */
+/* dR as well.                                                             */
 
 /* abar[v,k,b] += dx * ybin[v,b] * (B_v X)(k,b): the derivative of either
  * <qbar, A X> (forward) or <zbar, A^T y> (backward) with respect to the
@@ -403,10 +407,12 @@ static void accumulate_abar(const geom_t *g, const double *ybin,
     }
 }
 
-double orc_score_grad(int n, int nb, int V, double dx, double ds, double mu_b,
-                      double mu_c, double dR, const double *coef,
-                      const double *S, int K, int include_lgamma,
-                      double *grad, double *F_out)
+/* Forward pass and reverse sweep: returns L and fills mubar[n*n] with
+ * dL/dmu at every pixel (the caller owns mubar).                          */
+static double score_mubar(int n, int nb, int V, double dx, double ds,
+                          double mu_b, double mu_c, double dR,
+                          const double *coef, const double *S, int K,
+                          int include_lgamma, double *mubar, double *F_out)
 {
     geom_t g = {n, nb, V, dx, ds};
     int npix = n * n, nbin = V * nb;
@@ -496,7 +502,7 @@ double orc_score_grad(int n, int nb, int V, double dx, double ds, double mu_b,
     /* a = exp(-dx (m_k / 2 + sum_{k'>k} m_k')):
      * mbar_j = -dx (abar_j a_j / 2 + sum_{k<j} abar_k a_k).
      * mu samples are bilinear in mu, so mubar = sum_v B_v^T mbar_v.      */
-    double *mubar = calloc(npix, sizeof(double));
+    for (int j = 0; j < npix; ++j) mubar[j] = 0.0;
     for (int v = 0; v < V; ++v) {
         double cs, sn;
         view_cos_sin(v, V, &cs, &sn);
@@ -514,13 +520,39 @@ double orc_score_grad(int n, int nb, int V, double dx, double ds, double mu_b,
         }
     }
 
-    /* Eq. 4 (AREA) and Eq. 3: mu = (mu_b - mu_c) f(R) + mu_c f(R + dR). */
-    for (int k = 0; k < 6; ++k) grad[k] = 0.0;
+    free(mu); free(a); free(sens); free(F); free(q); free(r); free(z);
+    free(abar); free(Fbar); free(Fbar_new); free(sensbar); free(zbar);
+    free(qbar); free(rbar); free(tmp);
+    return L;
+}
+
+/* Chain rule through Eq. 4 (AREA) and Eq. 3:
+ *   mu = mu_b f(R) + mu_c (f(R + dR) - f(R)),  R = max(0, sum c_k P_k(z)),
+ *   f(R') = clamp(1/2 + (R' - r)/dx, 0, 1), f' = 1/dx strictly inside the ramp,
+ *   dmu/dc_k  = ((mu_b - mu_c) f'(R) + mu_c f'(R + dR)) P_k(z)   [R > 0]
+ *   dmu/dmu_b = f(R),  dmu/dmu_c = f(R + dR) - f(R),
+ *   dmu/ddR   = mu_c f'(R + dR)                                  [dR > 0].
+ * gc[6] always; gt[3] = (d/dmu_b, d/dmu_c, d/ddR) when not NULL.         */
+static void grad_from_mubar(int n, double dx, double mu_b, double mu_c,
+                            double dR, const double *coef,
+                            const double *mubar, double *gc, double *gt)
+{
+    for (int k = 0; k < 6; ++k) gc[k] = 0.0;
+    if (gt) gt[0] = gt[1] = gt[2] = 0.0;
     for (int i = 0; i < n; ++i)
         for (int j = 0; j < n; ++j) {
             double rr, zz;
             pixel_polar(n, dx, i, j, &rr, &zz);
             double Rraw = boundary_raw(coef, zz);
+            double mb = mubar[i * n + j];
+            if (gt) {
+                double R = Rraw > 0.0 ? Rraw : 0.0;
+                double fin = ramp(R, rr, dx), fout = ramp(R + dR, rr, dx);
+                double e_out = 0.5 + (R + dR - rr) / dx;
+                gt[0] += mb * fin;
+                gt[1] += mb * (fout - fin);
+                if (dR > 0.0 && e_out > 0.0 && e_out < 1.0) gt[2] += mb * mu_c / dx;
+            }
             if (!(Rraw > 0.0)) continue;
             double R = Rraw;
             double e_in = 0.5 + (R - rr) / dx, e_out = 0.5 + (R + dR - rr) / dx;
@@ -530,13 +562,37 @@ double orc_score_grad(int n, int nb, int V, double dx, double ds, double mu_b,
             if (dmu_dR == 0.0) continue;
             double P[6];
             orc_legendre(zz, P);
-            double s = mubar[i * n + j] * dmu_dR;
-            for (int k = 0; k < 6; ++k) grad[k] += s * P[k];
+            double s = mb * dmu_dR;
+            for (int k = 0; k < 6; ++k) gc[k] += s * P[k];
         }
+}
 
-    free(mu); free(a); free(sens); free(F); free(q); free(r); free(z);
-    free(abar); free(Fbar); free(Fbar_new); free(sensbar); free(zbar);
-    free(qbar); free(rbar); free(tmp); free(mubar);
+/* Score and dL/dc_0..c_5 for fixed tissue values.                         */
+double orc_score_grad(int n, int nb, int V, double dx, double ds, double mu_b,
+                      double mu_c, double dR, const double *coef,
+                      const double *S, int K, int include_lgamma,
+                      double *grad, double *F_out)
+{
+    double *mubar = malloc(sizeof(double) * n * n);
+    double L = score_mubar(n, nb, V, dx, ds, mu_b, mu_c, dR, coef, S, K,
+                           include_lgamma, mubar, F_out);
+    grad_from_mubar(n, dx, mu_b, mu_c, dR, coef, mubar, grad, NULL);
+    free(mubar);
+    return L;
+}
+
+/* The 9-parameter form p = (c_0..c_5, mu_b, mu_c, dR): score and dL/dp.
+ * A negative dR is taken as 0 (the map of dR = 0, derivative 0).          */
+double orc_score_grad_params(int n, int nb, int V, double dx, double ds,
+                             const double *p, const double *S, int K,
+                             int include_lgamma, double *grad, double *F_out)
+{
+    double dR = p[8] > 0.0 ? p[8] : 0.0;
+    double *mubar = malloc(sizeof(double) * n * n);
+    double L = score_mubar(n, nb, V, dx, ds, p[6], p[7], dR, p, S, K,
+                           include_lgamma, mubar, F_out);
+    grad_from_mubar(n, dx, p[6], p[7], dR, p, mubar, grad, grad + 6);
+    free(mubar);
     return L;
 }
 

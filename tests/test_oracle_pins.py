@@ -360,3 +360,63 @@ def test_gradient_against_central_differences():
     fd = np.array([fd_score(g, coef, S, K, 1e-4, k) for k in range(6)])
     scale = np.abs(fd).max()
     np.testing.assert_allclose(grad, fd, rtol=1e-3, atol=1e-3 * scale)
+
+
+def fd_score_params(g, p, S, K, h, k):
+    def L(pv):
+        dR = max(pv[8], 0.0)
+        mu = oracle.rasterize(g.n, g.dx, pv[6], pv[7], dR, pv[:6], oracle.AREA)
+        F = oracle.mlem(g, mu, S, K)
+        return oracle.score(g, mu, S, F)
+    e = np.zeros(9); e[k] = h
+    return (L(p + e) - L(p - e)) / (2 * h)
+
+
+def test_nine_parameter_gradient_against_central_differences():
+    """P8b: the 9-parameter form p = (c, mu_b, mu_c, dR) -- reverse-mode dL/dp
+    vs central finite differences of rasterize(AREA) -> MLEM -> score with the
+    tissue values moved too; its first six entries and L are those of the
+    6-coefficient gradient at the same tissue values."""
+    g, _, S, _ = small_problem(n=32, V=16, counts=2e5, seed=2)
+    K = 3
+    coef = np.array(synth.C_TRUE) + np.array([0.3, -0.1, 0.15, 0.05, 0.02, -0.03])
+    tissue = (0.13, 0.28, 0.75)
+    p = np.concatenate([coef, tissue])
+    L, grad, FK = oracle.score_grad_params(g, p, S, K)
+    L6, grad6, FK6 = oracle.score_grad(g, tissue, coef, S, K)
+    assert L == L6 and np.array_equal(grad[:6], grad6) and np.array_equal(FK, FK6)
+    fd = np.array([fd_score_params(g, p, S, K, 1e-4, k) for k in range(9)])
+    # each group on its own scale: cm for c and dR, cm^-1 for mu_b and mu_c
+    for sl in (slice(0, 6), slice(6, 8), slice(8, 9)):
+        scale = np.abs(fd[sl]).max()
+        assert scale > 0
+        np.testing.assert_allclose(grad[sl], fd[sl], rtol=1e-3, atol=1e-3 * scale)
+
+
+def test_nine_parameter_gradient_identities():
+    """With mu_b = mu_c the map is mu_b f(R + dR): moving c_0 (P_0 = 1) and
+    moving dR shift the same outer boundary, so dL/dc_0 = dL/ddR exactly as
+    long as R > 0 everywhere (a wrong factor or a dropped mu_c in the dR
+    term fails this).  A negative dR is taken as 0: same score as dR = 0 and
+    no derivative in dR."""
+    g, _, S, _ = small_problem(n=32, V=16, counts=2e5, seed=3)
+    K = 2
+    coef = np.array(synth.C_TRUE) + np.array([0.2, 0.1, -0.1, 0.0, 0.03, 0.0])
+    p = np.concatenate([coef, [0.2, 0.2, 0.5]])
+    _, grad, _ = oracle.score_grad_params(g, p, S, K)
+    assert grad[8] != 0.0
+    assert grad[0] == pytest.approx(grad[8], rel=1e-10)
+    # dL/dmu_b + dL/dmu_c is the derivative along mu_b = mu_c (one map value)
+    def L_at(m):
+        q = p.copy(); q[6] = q[7] = m
+        mu = oracle.rasterize(g.n, g.dx, m, m, q[8], q[:6], oracle.AREA)
+        return oracle.score(g, mu, S, oracle.mlem(g, mu, S, K))
+    h = 1e-4
+    fd = (L_at(0.2 + h) - L_at(0.2 - h)) / (2 * h)
+    assert grad[6] + grad[7] == pytest.approx(fd, rel=1e-5)
+    pneg = p.copy(); pneg[8] = -0.3
+    pzero = p.copy(); pzero[8] = 0.0
+    Ln, gn, _ = oracle.score_grad_params(g, pneg, S, K)
+    Lz, gz, _ = oracle.score_grad_params(g, pzero, S, K)
+    assert Ln == Lz and gn[8] == 0.0 and gz[8] == 0.0
+    np.testing.assert_array_equal(gn[:8], gz[:8])
