@@ -559,21 +559,30 @@ def run_workload(args):
         batch.prepare(config)
         ms = _timed(lambda: (batch.F_pool.fill_(1.0), batch.run()), dev, reps=1 if name == "large" else 2)
         extra = {"launch_config": config}
-    elif name == "grad":
+    elif name in ("grad", "grad_params"):
         wl = synth.GRAD
         g, t, (S,) = _phantom_sinograms(boac, Geom, Tissue, dev, wl.n, wl.dx, wl.V, wl.counts, [wl.seed])
-        c = torch.tensor(synth.candidates(synth.streams(wl.seed)[2], wl.B).astype(np.float32), device=dev)
+        c_np = synth.candidates(synth.streams(wl.seed)[2], wl.B)
         ck = wl.extra["ckpt_every"]
-        ms = _timed(lambda: boac.boac_score_grad(g, t, c, S, wl.K, ck), dev)
+        if name == "grad":
+            c = torch.tensor(c_np.astype(np.float32), device=dev)
+            ms = _timed(lambda: boac.boac_score_grad(g, t, c, S, wl.K, ck), dev)
+            what = "d lnP/dc"
+        else:
+            # per-candidate tissue values: the 9-parameter model
+            tis = synth.tissue_candidates(np.random.default_rng(wl.seed), wl.B)
+            prm = torch.tensor(np.concatenate([c_np, tis], 1).astype(np.float32), device=dev)
+            ms = _timed(lambda: boac.boac_score_grad_params(g, prm, S, wl.K, ck), dev)
+            what = "d lnP/d(c, mu_b, mu_c, dR), tissue values per candidate,"
         # forward MLEM, recomputation of each checkpoint segment, and the
         # adjoint iteration (two projections, two back-projections, the
         # attenuation adjoint): about 4 MLEM iterations of work per iteration
         work = [(wl.V, wl.n, 4 * wl.K)] * wl.B
         extra = {"work_model_note": "4 MLEM-iteration equivalents per differentiated iteration"}
-        desc = f"{wl.name}: {wl.B} candidates, d lnP/dc through {wl.K} iterations, checkpoint every {ck}"
+        desc = f"{wl.name}: {wl.B} candidates, {what} through {wl.K} iterations, checkpoint every {ck}"
     else:
         raise SystemExit(f"unknown workload {name}")
-    cand_its = sum(k for _, _, k in work) if name != "grad" else wl.B * wl.K
+    cand_its = sum(k for _, _, k in work) if not name.startswith("grad") else wl.B * wl.K
     flops = sum(FLOPS_PER_SAMPLE * V * n * n * k for V, n, k in work)
     line = {"metric": f"MLEM candidate-iterations/sec ({name} workload)", "value": cand_its / (ms / 1e3),
             "unit": UNIT, "n_gpus": 1, "ms": ms, "higher_is_better": True, "dtype": "f32",
@@ -599,7 +608,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffer) timing")
     ap.add_argument("--slices", type=int, default=0, help="large workload: slices (default 64)")
     ap.add_argument("--wl-iters", type=int, default=0, help="large workload: MLEM iterations (default 100)")
-    ap.add_argument("--workload", default="batched", choices=["batched", "small", "ragged", "large", "grad"],
+    ap.add_argument("--workload", default="batched", choices=["batched", "small", "ragged", "large", "grad", "grad_params"],
                     help="batched: the benchmark; the others print their own throughput line")
     ap.add_argument("--no-tune", action="store_true", help="ragged/large: default launch shapes")
     args = ap.parse_args()

@@ -118,6 +118,17 @@ size_t boac_workspace_bytes(const boac_geom *g, int B, int op);
 int boac_rasterize_mu(const boac_geom *g, const boac_tissue *t, const float *c,
                       int B, int mode, float *mu, void *stream);
 
+/* ---- Eq. 3-4 with per-candidate tissue values ----------------------------
+ * The 9-parameter model p = (c_0..c_5, mu_b, mu_c, dR): the paper fixes
+ * mu_b, mu_c and dR (Sec. II); here they may differ between candidates so
+ * that an optimiser can move them too.  Same maps as boac_rasterize_mu.
+ *   p   [B][9]     float32 (device): coefficients in cm, mu_b and mu_c in
+ *                  cm^-1, dR in cm; a negative or NaN dR is taken as 0
+ *   mu  [B][n][n]  output, cm^-1 (device, float32)
+ * Errors: BOAC_EINVAL for null pointers, B < 1, bad mode or geometry. */
+int boac_rasterize_mu_params(const boac_geom *g, const float *p, int B,
+                             int mode, float *mu, void *stream);
+
 /* ---- Eq. 1-2: forward projection q = A^mu F ----------------------------
  *   mu  [B][n][n], F [B][n][n]   (device, float32)
  *   q   [B][n_views][n_bins]     output (device, float32)
@@ -272,6 +283,22 @@ int boac_score_grad(const boac_geom *g, const boac_tissue *t, const float *c,
                     const float *S, long long s_stride, int K, int ckpt_every,
                     int B, int include_lgamma, double *L, double *dL_dc,
                     float *F_out, void *ws, size_t ws_bytes, void *stream);
+
+/* The same score and its gradient in the 9-parameter model (see
+ * boac_rasterize_mu_params): p [B][9] float32 (device) in, dL_dp [B][9]
+ * float64 (device) out, in the order c_0..c_5, mu_b, mu_c, dR.  Through the
+ * AREA map:
+ *   dmu/dmu_b = f(R),  dmu/dmu_c = f(R + dR) - f(R),
+ *   dmu/ddR   = mu_c f'(R + dR), taken as 0 where dR <= 0,
+ * f' = 1/pixel_cm strictly inside a ramp and 0 elsewhere.  The first six
+ * entries equal boac_score_grad's at the same tissue values.  Same
+ * workspace (boac_score_grad_workspace_bytes), outputs and errors as
+ * boac_score_grad. */
+int boac_score_grad_params(const boac_geom *g, const float *p, const float *S,
+                           long long s_stride, int K, int ckpt_every, int B,
+                           int include_lgamma, double *L, double *dL_dp,
+                           float *F_out, void *ws, size_t ws_bytes,
+                           void *stream);
 
 /* Eq. 5 reduction alone, for expected counts q already on the device:
  *   q [B][n_views][n_bins] float32, S as above, L [B] float64 output. */

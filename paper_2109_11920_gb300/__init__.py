@@ -13,8 +13,9 @@ from ._lib import (BOAC_EINVAL, BOAC_EUNSUPPORTED, BOAC_EWORKSPACE, BOAC_OK, OP_
 
 __all__ = [
     "Geom", "Tissue", "BoacError", "RASTER_CENTER", "RASTER_AREA",
-    "boac_rasterize_mu", "boac_project", "boac_backproject", "boac_mlem", "boac_mlem_plain",
-    "boac_score", "boac_loglik", "boac_workspace_bytes",
+    "boac_rasterize_mu", "boac_rasterize_mu_params", "boac_project", "boac_backproject",
+    "boac_mlem", "boac_mlem_plain", "boac_score", "boac_loglik", "boac_score_grad",
+    "boac_score_grad_params", "boac_workspace_bytes",
 ]
 
 

@@ -81,6 +81,7 @@ SIGNATURES = {
     "boac_workspace_status": (_I, [_P, _SZ, ctypes.POINTER(ctypes.c_int)]),
     "boac_workspace_bytes": (_SZ, [_GP, _I, _I]),
     "boac_rasterize_mu": (_I, [_GP, _TP, _P, _I, _I, _P, _P]),
+    "boac_rasterize_mu_params": (_I, [_GP, _P, _I, _I, _P, _P]),
     "boac_project": (_I, [_GP, _P, _P, _I, _P, _P]),
     "boac_backproject": (_I, [_GP, _P, _P, _I, _P, _P, _SZ, _P]),
     "boac_mlem": (_I, [_GP, _P, _P, _LL, _P, _I, _I, _P, _I, _P, _SZ, _P]),
@@ -96,6 +97,7 @@ SIGNATURES = {
     "boac_mlem_ragged": (_I, [_GP, _I, ctypes.POINTER(RaggedCand), _I, _P, _P, _P, _P, _I, _P, _P, _SZ,
                               _P]),
     "boac_score_grad": (_I, [_GP, _TP, _P, _P, _LL, _I, _I, _I, _I, _P, _P, _P, _P, _SZ, _P]),
+    "boac_score_grad_params": (_I, [_GP, _P, _P, _LL, _I, _I, _I, _I, _P, _P, _P, _P, _SZ, _P]),
 }
 
 

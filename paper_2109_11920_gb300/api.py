@@ -79,6 +79,21 @@ def boac_rasterize_mu(g: Geom, t: Tissue, c: torch.Tensor, mode: int = _lib.RAST
     return mu
 
 
+def boac_rasterize_mu_params(g: Geom, p: torch.Tensor, mode: int = _lib.RASTER_CENTER,
+                             out: torch.Tensor | None = None) -> torch.Tensor:
+    """Eq. 3-4 with per-candidate tissue values: mu[B, n, n] (cm^-1) from
+    p[B, 9] = (c_0..c_5 in cm, mu_b, mu_c in cm^-1, dR in cm)."""
+    _need(p, "p", torch.float32)
+    if p.dim() != 2 or p.shape[1] != 9:
+        raise ValueError("p must be [B, 9]")
+    B = p.shape[0]
+    mu = out if out is not None else torch.empty(B, g.n, g.n, dtype=torch.float32, device=p.device)
+    _need(mu, "mu", torch.float32, (B, g.n, g.n))
+    check("boac_rasterize_mu_params", _lib.load().boac_rasterize_mu_params(
+        ctypes.byref(g), _ptr(p), B, int(mode), _ptr(mu), _stream(p.device)))
+    return mu
+
+
 def boac_project(g: Geom, mu: torch.Tensor, F: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
     """Eq. 1-2: q[B, V, nb] = A^mu F."""
     _need(mu, "mu", torch.float32)
@@ -194,15 +209,46 @@ def boac_score_grad(g: Geom, t: Tissue, c: torch.Tensor, S: torch.Tensor, K: int
     return L, grad, F
 
 
+def boac_score_grad_params(g: Geom, p: torch.Tensor, S: torch.Tensor, K: int,
+                           ckpt_every: int = 2, include_lgamma: bool = True, want_image: bool = False,
+                           ws: torch.Tensor | None = None):
+    """boac_score_grad in the 9-parameter model p[B, 9] = (c_0..c_5, mu_b, mu_c,
+    dR): returns (L[B], dL/dp[B, 9], F^K or None), L and dL/dp in float64."""
+    _need(p, "p", torch.float32)
+    if p.dim() != 2 or p.shape[1] != 9:
+        raise ValueError("p must be [B, 9]")
+    B = p.shape[0]
+    S, stride = _sino(S, g, B)
+    lib = _lib.load()
+    if ws is None:
+        nbytes = int(lib.boac_score_grad_workspace_bytes(ctypes.byref(g), B, int(K), int(ckpt_every)))
+        if nbytes == 0:
+            raise ValueError("invalid arguments for boac_score_grad_params")
+        ws = torch.empty(nbytes, dtype=torch.uint8, device=p.device)
+    L = torch.empty(B, dtype=torch.float64, device=p.device)
+    grad = torch.empty(B, 9, dtype=torch.float64, device=p.device)
+    F = torch.empty(B, g.n, g.n, dtype=torch.float32, device=p.device) if want_image else None
+    check("boac_score_grad_params", lib.boac_score_grad_params(
+        ctypes.byref(g), _ptr(p), _ptr(S), stride, int(K), int(ckpt_every), B,
+        int(include_lgamma), _ptr(L), _ptr(grad), _ptr(F), _ptr(ws), ws.numel(), _stream(p.device)))
+    return L, grad, F
+
+
 class BoacScore(torch.autograd.Function):
     """ln P(S | F^K(c), A^mu(c)) as a differentiable function of the Legendre
-    coefficients c[B, 6]: the forward runs boac_score_grad (which returns the
-    gradient together with the score), the backward scales it by the incoming
-    gradient.  Usage: ``L = BoacScore.apply(c, geom, tissue, S, K, ckpt_every)``."""
+    coefficients c[B, 6] (tissue values t), or of the 9-parameter model
+    c[B, 9] = (c_0..c_5, mu_b, mu_c, dR) (t unused, may be None): the forward
+    runs boac_score_grad / boac_score_grad_params (which return the gradient
+    together with the score), the backward scales it by the incoming gradient.
+    Usage: ``L = BoacScore.apply(c, geom, tissue, S, K, ckpt_every)``."""
 
     @staticmethod
     def forward(ctx, c, g, t, S, K, ckpt_every=2, include_lgamma=True):
-        L, grad, _ = boac_score_grad(g, t, c.detach().contiguous(), S, K, ckpt_every, include_lgamma)
+        cd = c.detach().contiguous()
+        if cd.dim() == 2 and cd.shape[1] == 9:
+            L, grad, _ = boac_score_grad_params(g, cd, S, K, ckpt_every, include_lgamma)
+        else:
+            L, grad, _ = boac_score_grad(g, t, cd, S, K, ckpt_every, include_lgamma)
         ctx.save_for_backward(grad)
         ctx.c_dtype = c.dtype
         return L

@@ -220,7 +220,9 @@ class BOACOptimizer:
 
 def gpu_objective(g, t, S, K: int, device=None, include_lgamma: bool = False):
     """-ln P(S | F^K(c), A^mu(c)) for a batch of coefficient vectors, on the
-    GPU: rasterise (Eq. 3-4), K fused MLEM iterations, Eq. 5 score."""
+    GPU: rasterise (Eq. 3-4), K fused MLEM iterations, Eq. 5 score.  Rows of
+    6 are Legendre coefficients with the tissue values t; rows of 9 are the
+    9-parameter model (c_0..c_5, mu_b, mu_c, dR) and t is not used."""
     import torch
 
     from . import api
@@ -229,7 +231,10 @@ def gpu_objective(g, t, S, K: int, device=None, include_lgamma: bool = False):
 
     def evaluate(C: np.ndarray) -> np.ndarray:
         c = torch.tensor(np.asarray(C, dtype=np.float32), device=dev)
-        mu = api.boac_rasterize_mu(g, t, c)
+        if c.shape[1] == 9:
+            mu = api.boac_rasterize_mu_params(g, c)
+        else:
+            mu = api.boac_rasterize_mu(g, t, c)
         F = torch.ones(c.shape[0], g.n, g.n, device=dev)
         _, L = api.boac_mlem(g, mu, S, F, K, include_lgamma=include_lgamma)
         return (-L).cpu().numpy()

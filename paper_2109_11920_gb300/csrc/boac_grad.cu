@@ -221,16 +221,29 @@ __global__ void mlem_step_adjoint_kernel(long long count, const float* __restric
 // dL/dc_k = sum_pixels mubar dmu/dR P_k(z) for the AREA map
 //   mu = (mu_b - mu_c) f(R) + mu_c f(R + dR), f(R') = clamp(1/2 + (R'-r)/dx, 0, 1),
 //   R = max(0, sum c_k P_k(z)):  dmu/dR = ((mu_b - mu_c) f'(R) + mu_c f'(R+dR)) [R > 0],
+// and with NP = 9 (per-candidate tissue values after the coefficients) also
+//   dL/dmu_b = sum mubar f(R),  dL/dmu_c = sum mubar (f(R + dR) - f(R)),
+//   dL/ddR = sum mubar mu_c f'(R + dR) [dR > 0],
 // accumulated in float64 with a fixed reduction tree.  One block per candidate.
-__global__ void grad_coef_kernel(int n, double dx, double mu_b, double mu_c, double dR,
+template <int NP>
+__global__ void grad_coef_kernel(int n, double dx, double mu_b0, double mu_c0, double dR0,
                                  const float* __restrict__ coef, const float* __restrict__ mubar,
                                  double* __restrict__ grad) {
-    __shared__ double part[32][6];
+    __shared__ double part[32][NP];
     const int cand = blockIdx.x;
     double c6[6];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) c6[k] = (double)__ldg(coef + cand * 6 + k);
-    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int k = 0; k < 6; ++k) c6[k] = (double)__ldg(coef + cand * NP + k);
+    double mu_b = mu_b0, mu_c = mu_c0, dR = dR0;
+    if (NP == kParams) {
+        mu_b = (double)__ldg(coef + cand * NP + 6);
+        mu_c = (double)__ldg(coef + cand * NP + 7);
+        const double d = (double)__ldg(coef + cand * NP + 8);
+        dR = d > 0.0 ? d : 0.0;
+    }
+    double acc[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) acc[k] = 0.0;
     const double cc = 0.5 * (double)(n - 1);
     const float* mb = mubar + (size_t)cand * n * n;
     for (int pix = threadIdx.x; pix < n * n; pix += blockDim.x) {
@@ -246,6 +259,15 @@ __global__ void grad_coef_kernel(int n, double dx, double mu_b, double mu_c, dou
         double R = 0.0;
 #pragma unroll
         for (int k = 0; k < 6; ++k) R += c6[k] * P[k];
+        if (NP == kParams) {
+            const double m = (double)mb[pix];
+            const double Rc = R > 0.0 ? R : 0.0;
+            const double ein = 0.5 + (Rc - r) / dx, eout = 0.5 + (Rc + dR - r) / dx;
+            const double fin = fmin(fmax(ein, 0.0), 1.0), fout = fmin(fmax(eout, 0.0), 1.0);
+            acc[6] += m * fin;
+            acc[7] += m * (fout - fin);
+            if (dR > 0.0 && eout > 0.0 && eout < 1.0) acc[8] += m * mu_c / dx;
+        }
         if (!(R > 0.0)) continue;
         const double ein = 0.5 + (R - r) / dx, eout = 0.5 + (R + dR - r) / dx;
         const double din = (ein > 0.0 && ein < 1.0) ? 1.0 / dx : 0.0;
@@ -257,16 +279,16 @@ __global__ void grad_coef_kernel(int n, double dx, double mu_b, double mu_c, dou
         for (int k = 0; k < 6; ++k) acc[k] += s * P[k];
     }
 #pragma unroll
-    for (int k = 0; k < 6; ++k)
+    for (int k = 0; k < NP; ++k)
         for (int off = 16; off > 0; off >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], off);
     if ((threadIdx.x & 31) == 0)
 #pragma unroll
-        for (int k = 0; k < 6; ++k) part[threadIdx.x >> 5][k] = acc[k];
+        for (int k = 0; k < NP; ++k) part[threadIdx.x >> 5][k] = acc[k];
     __syncthreads();
-    if (threadIdx.x < 6) {
+    if (threadIdx.x < NP) {
         double t = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w][threadIdx.x];
-        grad[cand * 6 + threadIdx.x] = t;
+        grad[cand * NP + threadIdx.x] = t;
     }
 }
 
@@ -319,13 +341,13 @@ extern "C" size_t boac_score_grad_workspace_bytes(const boac_geom* g, int B, int
     return grad_layout(g, B, K, ckpt_every).total;
 }
 
-extern "C" int boac_score_grad(const boac_geom* g, const boac_tissue* t, const float* c,
-                               const float* S, long long s_stride, int K, int ckpt_every, int B,
-                               int include_lgamma, double* L, double* dL_dc, float* F_out, void* ws,
-                               size_t ws_bytes, void* stream) {
-    if (!geom_ok(g) || !t || !c || !S || !L || !dL_dc || B < 1 || B > 65535 || K < 0 ||
-        ckpt_every < 1 || s_stride < 0)
-        return BOAC_EINVAL;
+// Score and gradient of B candidates: t != nullptr takes c[B][6] with the
+// tissue values of t and writes dL_dc[B][6]; t == nullptr takes the
+// 9-parameter form c[B][9] and writes dL_dc[B][9].
+static int score_grad_run(const boac_geom* g, const boac_tissue* t, const float* c,
+                          const float* S, long long s_stride, int K, int ckpt_every, int B,
+                          int include_lgamma, double* L, double* dL_dc, float* F_out, void* ws,
+                          size_t ws_bytes, void* stream) {
     const GradLayout lay = grad_layout(g, B, K, ckpt_every);
     if (!ws || ws_bytes < lay.total) return BOAC_EWORKSPACE;
     char* base = static_cast<char*>(ws);
@@ -352,7 +374,7 @@ extern "C" int boac_score_grad(const boac_geom* g, const boac_tissue* t, const f
         update_kernel<<<g1p, 256, 0, st>>>((int)cnt_pix, F_o, z, sens);
     };
     // ---- forward
-    int s = boac_rasterize_mu(g, t, c, B, BOAC_RASTER_AREA, mu, stream);
+    int s = rasterize_launch(g, t, c, t ? 6 : kParams, B, BOAC_RASTER_AREA, mu, st);
     if (s != BOAC_OK) return s;
     attenuation_table_kernel<<<rg, kRayThreads, 0, st>>>(n, V, dx, mu, tab);
     backproject_table(g, B, tab, nullptr, dx, sens, 0, partial, st);
@@ -417,7 +439,32 @@ extern "C" int boac_score_grad(const boac_geom* g, const boac_tissue* t, const f
     // attenuation -> mu samples -> pixels -> coefficients
     mbar_kernel<<<rg, kRayThreads, 0, st>>>(n, V, dx, tab, abar);
     backproject_table(g, B, abar, nullptr, 1.0f, mubar, 0, partial, st);
-    grad_coef_kernel<<<B, 256, 0, st>>>(n, (double)dx, (double)t->mu_b, (double)t->mu_c, (double)t->dR, c,
-                                        mubar, dL_dc);
+    if (t)
+        grad_coef_kernel<6><<<B, 256, 0, st>>>(n, (double)dx, (double)t->mu_b, (double)t->mu_c,
+                                               (double)t->dR, c, mubar, dL_dc);
+    else
+        grad_coef_kernel<kParams><<<B, 256, 0, st>>>(n, (double)dx, 0.0, 0.0, 0.0, c, mubar, dL_dc);
     return launch_status();
+}
+
+extern "C" int boac_score_grad(const boac_geom* g, const boac_tissue* t, const float* c,
+                               const float* S, long long s_stride, int K, int ckpt_every, int B,
+                               int include_lgamma, double* L, double* dL_dc, float* F_out, void* ws,
+                               size_t ws_bytes, void* stream) {
+    if (!geom_ok(g) || !t || !c || !S || !L || !dL_dc || B < 1 || B > 65535 || K < 0 ||
+        ckpt_every < 1 || s_stride < 0 || !(t->dR >= 0.0f))
+        return BOAC_EINVAL;
+    return score_grad_run(g, t, c, S, s_stride, K, ckpt_every, B, include_lgamma, L, dL_dc, F_out,
+                          ws, ws_bytes, stream);
+}
+
+extern "C" int boac_score_grad_params(const boac_geom* g, const float* p, const float* S,
+                                      long long s_stride, int K, int ckpt_every, int B,
+                                      int include_lgamma, double* L, double* dL_dp, float* F_out,
+                                      void* ws, size_t ws_bytes, void* stream) {
+    if (!geom_ok(g) || !p || !S || !L || !dL_dp || B < 1 || B > 65535 || K < 0 ||
+        ckpt_every < 1 || s_stride < 0)
+        return BOAC_EINVAL;
+    return score_grad_run(g, nullptr, p, S, s_stride, K, ckpt_every, B, include_lgamma, L, dL_dp,
+                          F_out, ws, ws_bytes, stream);
 }

@@ -38,4 +38,12 @@ size_t backproject_candidate_bytes(const boac_geom* g);
 // Fused MLEM: workspace for geometry g and B candidates.
 size_t fused_workspace_bytes(const boac_geom* g, int B);
 
+// Entries per candidate of the 9-parameter model (c_0..c_5, mu_b, mu_c, dR).
+constexpr int kParams = 9;
+
+// Eq. 3-4 for B candidates: coefficients p[cand * pstride + 0..5]; pstride
+// 6 takes the tissue values from t, pstride kParams from p (t unused).
+int rasterize_launch(const boac_geom* g, const boac_tissue* t, const float* p, int pstride, int B,
+                     int mode, float* mu, cudaStream_t st);
+
 }  // namespace boac

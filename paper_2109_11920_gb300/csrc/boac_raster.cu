@@ -33,8 +33,11 @@ __device__ __forceinline__ double ramp(double Rp, double r, double dx) {
     return fmin(fmax(f, 0.0), 1.0);
 }
 
-__global__ void rasterize_kernel(int n, double dx, double mu_b, double mu_c, double dR,
-                                 const float* __restrict__ coef, int B, int mode,
+// Candidate cand's coefficients are coef[cand * pstride + 0..5]; with
+// pstride = 9 its tissue values follow them (mu_b, mu_c, dR; a negative or
+// NaN dR is taken as 0), with pstride = 6 every candidate uses the arguments.
+__global__ void rasterize_kernel(int n, double dx, double mu_b0, double mu_c0, double dR0,
+                                 const float* __restrict__ coef, int pstride, int B, int mode,
                                  float* __restrict__ mu) {
     const long long total = (long long)B * n * n;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
@@ -44,7 +47,15 @@ __global__ void rasterize_kernel(int n, double dx, double mu_b, double mu_c, dou
         const int i = pix / n, j = pix % n;
         double c6[6], P[6];
 #pragma unroll
-        for (int k = 0; k < 6; ++k) c6[k] = (double)__ldg(coef + cand * 6 + k);
+        for (int k = 0; k < 6; ++k) c6[k] = (double)__ldg(coef + (long long)cand * pstride + k);
+        double mu_b = mu_b0, mu_c = mu_c0, dR = dR0;
+        if (pstride == kParams) {
+            const float* t = coef + (long long)cand * kParams + 6;
+            mu_b = (double)__ldg(t);
+            mu_c = (double)__ldg(t + 1);
+            const double d = (double)__ldg(t + 2);
+            dR = d > 0.0 ? d : 0.0;
+        }
         const double cc = 0.5 * (double)(n - 1);
         const double x = __dmul_rn((double)j - cc, dx), y = __dmul_rn((double)i - cc, dx);
         const double r = __dsqrt_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)));
@@ -66,18 +77,35 @@ __global__ void rasterize_kernel(int n, double dx, double mu_b, double mu_c, dou
 
 using namespace boac;
 
-extern "C" int boac_rasterize_mu(const boac_geom* g, const boac_tissue* t, const float* c, int B,
-                                 int mode, float* mu, void* stream) {
-    if (!geom_ok(g) || !t || !c || !mu || B < 1) return BOAC_EINVAL;
-    if (mode != BOAC_RASTER_CENTER && mode != BOAC_RASTER_AREA) return BOAC_EINVAL;
-    if (!(t->dR >= 0.0f)) return BOAC_EINVAL;
+namespace boac {
+
+int rasterize_launch(const boac_geom* g, const boac_tissue* t, const float* p, int pstride, int B,
+                     int mode, float* mu, cudaStream_t st) {
     long long total = (long long)B * g->n * g->n;
     int threads = 256;
     long long blocks = (total + threads - 1) / threads;
     long long cap = 64LL * (sm_count() > 0 ? sm_count() : 1);
     if (blocks > cap) blocks = cap;
-    rasterize_kernel<<<(int)blocks, threads, 0, as_stream(stream)>>>(
-        g->n, (double)g->pixel_cm, (double)t->mu_b, (double)t->mu_c, (double)t->dR, c, B, mode,
-        mu);
+    const double mu_b = t ? (double)t->mu_b : 0.0, mu_c = t ? (double)t->mu_c : 0.0,
+                 dR = t ? (double)t->dR : 0.0;
+    rasterize_kernel<<<(int)blocks, threads, 0, st>>>(g->n, (double)g->pixel_cm, mu_b, mu_c, dR, p,
+                                                      pstride, B, mode, mu);
     return launch_status();
+}
+
+}  // namespace boac
+
+extern "C" int boac_rasterize_mu(const boac_geom* g, const boac_tissue* t, const float* c, int B,
+                                 int mode, float* mu, void* stream) {
+    if (!geom_ok(g) || !t || !c || !mu || B < 1) return BOAC_EINVAL;
+    if (mode != BOAC_RASTER_CENTER && mode != BOAC_RASTER_AREA) return BOAC_EINVAL;
+    if (!(t->dR >= 0.0f)) return BOAC_EINVAL;
+    return rasterize_launch(g, t, c, 6, B, mode, mu, as_stream(stream));
+}
+
+extern "C" int boac_rasterize_mu_params(const boac_geom* g, const float* p, int B, int mode,
+                                        float* mu, void* stream) {
+    if (!geom_ok(g) || !p || !mu || B < 1) return BOAC_EINVAL;
+    if (mode != BOAC_RASTER_CENTER && mode != BOAC_RASTER_AREA) return BOAC_EINVAL;
+    return rasterize_launch(g, nullptr, p, kParams, B, mode, mu, as_stream(stream));
 }

@@ -102,6 +102,13 @@ def candidates(rng: np.random.Generator, B: int, c_true=C_TRUE,
     return c[None, :] + rng.normal(size=(B, 6)) * sd[None, :]
 
 
+def tissue_candidates(rng: np.random.Generator, B: int, tissue=TISSUE,
+                      spread: float = 0.2) -> np.ndarray:
+    """B (mu_b, mu_c, dR) triples, each value times U(1 - spread, 1 + spread)."""
+    t = np.asarray(tissue, dtype=np.float64)
+    return t[None, :] * rng.uniform(1.0 - spread, 1.0 + spread, (B, 3))
+
+
 def ragged_schedule(rng: np.random.Generator, B: int = 512, mix=(1, 1, 2), k_range=(20, 80)):
     """Size class per candidate in the given ratio (shuffled) and iteration
     counts uniform on k_range (inclusive)."""
