@@ -559,6 +559,23 @@ def run_workload(args):
         batch.prepare(config)
         ms = _timed(lambda: (batch.F_pool.fill_(1.0), batch.run()), dev, reps=1 if name == "large" else 2)
         extra = {"launch_config": config}
+    elif name == "quality":
+        from paper_2109_11920_gb300 import quality
+        wl = quality.QUALITY
+        rows, t0 = [], time.perf_counter()
+        for case in range(wl.extra["cases"]):
+            r = quality.run_case(case, dev)
+            rows.append({"case": case, "c_true": [round(float(x), 4) for x in r["c_true"]],
+                         "c_bo": [round(float(x), 4) for x in r["c_bo"]],
+                         "scores": {k: {m: round(v, 4) for m, v in sc.items()} for k, sc in r["scores"].items()}})
+        wall = time.perf_counter() - t0
+        print(json.dumps({"metric": "SSIM / CNR / PSNR of MLEM-BOAC vs MLEM-NAC (quality workload)",
+                          "unit": "score", "n_gpus": 1, "wall_s": wall, "data": "synthetic",
+                          "config": {"workload": f"{wl.name}: {wl.extra['cases']} seeded heads, {wl.n}x{wl.n}, "
+                                                 f"{wl.V} views, {wl.counts:g} counts, K={wl.K}, BO {wl.extra['bo_init']} "
+                                                 f"initial + {wl.extra['bo_cycles']} cycles x {wl.B} candidates"},
+                          "cases": rows}), flush=True)
+        return
     elif name in ("grad", "grad_params"):
         wl = synth.GRAD
         g, t, (S,) = _phantom_sinograms(boac, Geom, Tissue, dev, wl.n, wl.dx, wl.V, wl.counts, [wl.seed])
@@ -608,7 +625,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffer) timing")
     ap.add_argument("--slices", type=int, default=0, help="large workload: slices (default 64)")
     ap.add_argument("--wl-iters", type=int, default=0, help="large workload: MLEM iterations (default 100)")
-    ap.add_argument("--workload", default="batched", choices=["batched", "small", "ragged", "large", "grad", "grad_params"],
+    ap.add_argument("--workload", default="batched", choices=["batched", "small", "ragged", "large", "grad", "grad_params", "quality"],
                     help="batched: the benchmark; the others print their own throughput line")
     ap.add_argument("--no-tune", action="store_true", help="ragged/large: default launch shapes")
     args = ap.parse_args()
