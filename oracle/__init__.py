@@ -68,6 +68,7 @@ def _load():
             lib.orc_score.restype = Dv
             lib.orc_score_grad.argtypes = geo + [Dv, Dv, Dv, D, D, I, I, D, D]
             lib.orc_score_grad.restype = Dv
+            lib.orc_system_matrix.argtypes = geo + [D, D]
             lib.orc_score_grad_params.argtypes = geo + [D, D, I, I, D, D]
             lib.orc_score_grad_params.restype = Dv
             lib.orc_mlem_batch.argtypes = geo + [I, D, D, ctypes.c_longlong,
@@ -188,6 +189,14 @@ def score_grad(g: Geometry, tissue, coef, S, K: int, include_lgamma: bool = True
     L = _load().orc_score_grad(*g.args, mu_b, mu_c, dR, _d(c), _d(S), int(K),
                                int(include_lgamma), _d(grad), _d(F))
     return L, grad, F
+
+
+def system_matrix(g: Geometry, mu) -> np.ndarray:
+    """Dense A^mu [V * nb, n * n]: row (v, b), column i * n + j."""
+    mu = _arr(mu, (g.n, g.n))
+    A = np.zeros((g.V * g.nb, g.n * g.n))
+    _load().orc_system_matrix(*g.args, _d(mu), _d(A))
+    return A
 
 
 def score_grad_params(g: Geometry, params, S, K: int, include_lgamma: bool = True):

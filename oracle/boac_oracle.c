@@ -274,6 +274,42 @@ void orc_project(int n, int nb, int V, double dx, double ds, const double *mu,
     }
 }
 
+/* The system matrix A^mu written out (Sec. III: the "system matrix" linking
+ * F to the sinogram, Eq. 2): A[(v*nb + b)*n*n + i*n + j] = dx * sum_k a_k w_k,
+ * w_k the bilinear weight with which sample k of ray (v, b) reads pixel
+ * (i, j), a_k its attenuation factor.  Dense, row-major [V*nb][n*n].       */
+void orc_system_matrix(int n, int nb, int V, double dx, double ds,
+                       const double *mu, double *A)
+{
+    geom_t g = {n, nb, V, dx, ds};
+    size_t npix = (size_t)n * n;
+    double *a = malloc(sizeof(double) * (size_t)V * n * nb);
+    attenuation_table(&g, mu, a);
+    memset(A, 0, sizeof(double) * (size_t)V * nb * npix);
+    for (int v = 0; v < V; ++v) {
+        double cs, sn;
+        view_cos_sin(v, V, &cs, &sn);
+        for (int b = 0; b < nb; ++b) {
+            double *row = A + ((size_t)v * nb + b) * npix;
+            for (int k = 0; k < n; ++k) {
+                double u, w;
+                ray_uw(&g, cs, sn, k, b, &u, &w);
+                double j0f = floor(u), i0f = floor(w);
+                double au = u - j0f, aw = w - i0f;
+                double ak = a[((size_t)v * n + k) * nb + b];
+                for (int di = 0; di < 2; ++di)
+                    for (int dj = 0; dj < 2; ++dj) {
+                        int i = (int)i0f + di, j = (int)j0f + dj;
+                        if (i < 0 || i >= n || j < 0 || j >= n) continue;
+                        double wt = (di ? aw : 1.0 - aw) * (dj ? au : 1.0 - au);
+                        row[(size_t)i * n + j] += dx * ak * wt;
+                    }
+            }
+        }
+    }
+    free(a);
+}
+
 /* Public back-projector: the explicit transpose of orc_project.          */
 void orc_backproject(int n, int nb, int V, double dx, double ds,
                      const double *mu, const double *y, double *out)

@@ -252,6 +252,28 @@ def test_dense_brute_force_16():
     np.testing.assert_allclose(oracle.sensitivity(g, mu).ravel(), A.sum(axis=0), rtol=1e-13, atol=1e-14)
 
 
+def test_system_matrix_written_out():
+    """P5b: the oracle's explicit A^mu (the system matrix of Sec. III) equals
+    the hat-function brute force above, its products equal the matrix-free
+    projector and back-projector, every entry is >= 0 and no row has more
+    than 4n nonzeros (four bilinear neighbours per sample)."""
+    n, V = 16, 8
+    dx = 25.6 / n
+    mu = oracle.rasterize(n, dx, MU_B, MU_C, DR, [6.5, 0.4, -0.5, 0.2, -0.1, 0.05], oracle.CENTER)
+    g = oracle.Geometry(n, dx, V)
+    A = oracle.system_matrix(g, mu)
+    np.testing.assert_allclose(A, dense_system_matrix(n, dx, V, mu), rtol=1e-12, atol=1e-14)
+    assert A.min() >= 0.0 and (A > 0).sum(axis=1).max() <= 4 * n
+    g = oracle.Geometry(24, 0.6, 12)
+    mu = oracle.rasterize(24, 0.6, MU_B, MU_C, DR, [6.0, 0.3, -0.4, 0.1, 0.0, 0.05], oracle.AREA)
+    A = oracle.system_matrix(g, mu)
+    rng = np.random.default_rng(6)
+    x = rng.uniform(0, 2, (24, 24))
+    y = rng.uniform(0, 2, (12, 24))
+    np.testing.assert_allclose(A @ x.ravel(), oracle.project(g, mu, x).ravel(), rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(A.T @ y.ravel(), oracle.backproject(g, mu, y).ravel(), rtol=1e-12, atol=1e-14)
+
+
 def test_mirror_symmetry():
     """P7: with a head symmetric about the x axis (P_k(cos theta) is even in
     theta) and a mirror-symmetric activity, q(v, b) = q((V/2 - v) mod V,
