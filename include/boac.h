@@ -300,6 +300,57 @@ int boac_score_grad_params(const boac_geom *g, const float *p, const float *S,
                            float *F_out, void *ws, size_t ws_bytes,
                            void *stream);
 
+/* ---- The system matrix A^mu written out (Sec. III) ----------------------
+ * The explicit-matrix counterpart of the matrix-free path, for comparison:
+ * A[(v, b)][p] = pixel_cm * sum_k a_k w_k(p) over the ray samples k of bin b
+ * of view v that read pixel p = i * n + j with bilinear weight w_k(p) (the
+ * same samples, weights and attenuation factors as boac_project).  Rows
+ * R = n_views * n_bins, columns n * n.
+ *
+ * Which pixels a row reads depends on the geometry only, so a boac_sysmat
+ * holds one sparsity pattern, shared by every candidate: CSR row pointers
+ * [R + 1] and column indices [nnz] (ascending within a row), and the CSR of
+ * A^T (pixel pointers [n * n + 1], row indices [nnz], ascending).  Entries
+ * whose weight happens to be exactly 0 are kept.  Values are per candidate,
+ * interleaved by groups of 8 candidates so that one entry of a group is one
+ * 32-byte sector: vals [G][2][nnz][8] float32, G = ceil(B / 8), with
+ * vals[b / 8][0][e][b % 8] entry e of candidate b in the order of A and
+ * vals[b / 8][1][e][b % 8] the same values in the order of A^T (zeros for
+ * the candidates of the last group beyond B).
+ *
+ * boac_sysmat_create builds the pattern on the device (device memory of
+ * about 16 bytes per nonzero, about 2 n nonzeros per row) and synchronises
+ * `stream` twice; the caller owns the handle and frees it with
+ * boac_sysmat_destroy.  Errors: BOAC_EINVAL (geometry, null out),
+ * BOAC_ECUDA (allocation or launch), BOAC_EUNSUPPORTED (a consistency
+ * check of the build failed, or a pixel is read by more than 4096 rows).
+ * boac_sysmat_nnz returns the number of nonzeros (-1 for a null handle).
+ * boac_sysmat_pattern copies the pattern into caller device buffers (any
+ * may be NULL).
+ * boac_sysmat_values fills vals for B candidates from mu [B][n][n]
+ * (16-byte aligned).
+ * boac_sysmat_project: q [B][R] = A F for F [B][n][n].
+ * boac_sysmat_mlem: K MLEM iterations on F [B][n][n] in place (sens = A^T 1,
+ * F <- F A^T(S / A F) / sens with the conventions of boac_mlem) and, when
+ * L is not NULL, the Eq. 5 score of the result (float64 [B]); S and
+ * s_stride as for boac_mlem; ws boac_sysmat_mlem_workspace_bytes(m, B)
+ * bytes.  Deterministic: every sum runs in a fixed order. */
+typedef struct boac_sysmat boac_sysmat;
+int boac_sysmat_create(const boac_geom *g, boac_sysmat **out, void *stream);
+int boac_sysmat_destroy(boac_sysmat *m);
+long long boac_sysmat_nnz(const boac_sysmat *m);
+int boac_sysmat_pattern(const boac_sysmat *m, int *row_ptr, int *col,
+                        int *colT_ptr, int *rowT, void *stream);
+int boac_sysmat_values(const boac_sysmat *m, const float *mu, int B,
+                       float *vals, void *stream);
+int boac_sysmat_project(const boac_sysmat *m, const float *vals,
+                        const float *F, int B, float *q, void *stream);
+size_t boac_sysmat_mlem_workspace_bytes(const boac_sysmat *m, int B);
+int boac_sysmat_mlem(const boac_sysmat *m, const float *vals, const float *S,
+                     long long s_stride, float *F, int K, int B, double *L,
+                     int include_lgamma, void *ws, size_t ws_bytes,
+                     void *stream);
+
 /* Eq. 5 reduction alone, for expected counts q already on the device:
  *   q [B][n_views][n_bins] float32, S as above, L [B] float64 output. */
 int boac_loglik(const boac_geom *g, const float *q, const float *S,

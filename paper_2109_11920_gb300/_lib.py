@@ -98,6 +98,14 @@ SIGNATURES = {
                               _P]),
     "boac_score_grad": (_I, [_GP, _TP, _P, _P, _LL, _I, _I, _I, _I, _P, _P, _P, _P, _SZ, _P]),
     "boac_score_grad_params": (_I, [_GP, _P, _P, _LL, _I, _I, _I, _I, _P, _P, _P, _P, _SZ, _P]),
+    "boac_sysmat_create": (_I, [_GP, ctypes.POINTER(_P), _P]),
+    "boac_sysmat_destroy": (_I, [_P]),
+    "boac_sysmat_nnz": (_LL, [_P]),
+    "boac_sysmat_pattern": (_I, [_P, _P, _P, _P, _P, _P]),
+    "boac_sysmat_values": (_I, [_P, _P, _I, _P, _P]),
+    "boac_sysmat_project": (_I, [_P, _P, _P, _I, _P, _P]),
+    "boac_sysmat_mlem_workspace_bytes": (_SZ, [_P, _I]),
+    "boac_sysmat_mlem": (_I, [_P, _P, _P, _LL, _P, _I, _I, _P, _I, _P, _SZ, _P]),
 }
 
 

@@ -234,6 +234,96 @@ def boac_score_grad_params(g: Geom, p: torch.Tensor, S: torch.Tensor, K: int,
     return L, grad, F
 
 
+class SysMat:
+    """The system matrix A^mu written out (boac_sysmat_*): one sparsity pattern
+    per geometry, values per candidate.  ``vals = m.values(mu)`` gives
+    [ceil(B/8), 2, nnz, 8] float32 (groups of 8 candidates interleaved; A's
+    order, then A^T's; ``SysMat.candidate_values(vals, b)`` extracts one);
+    ``m.mlem(vals, S, F, K)`` runs MLEM on it; ``m.project(vals, F)`` is
+    q = A F; ``m.pattern()`` returns (row_ptr, col, colT_ptr, rowT) as int32
+    device tensors."""
+
+    GROUP = 8
+
+    @staticmethod
+    def vals_shape(B: int, nnz: int):
+        return ((B + SysMat.GROUP - 1) // SysMat.GROUP, 2, nnz, SysMat.GROUP)
+
+    @staticmethod
+    def candidate_values(vals: torch.Tensor, b: int) -> torch.Tensor:
+        """[2, nnz] values of candidate b (A's order, then A^T's)."""
+        return vals[b // SysMat.GROUP, :, :, b % SysMat.GROUP]
+
+    def __init__(self, g: Geom, device=None):
+        self.g = g
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self._lib = _lib.load()
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            check("boac_sysmat_create", self._lib.boac_sysmat_create(ctypes.byref(g), ctypes.byref(h),
+                                                                     _stream(self.device)))
+        self._h = h
+        self.nnz = int(self._lib.boac_sysmat_nnz(h))
+        self.rows = g.n_views * g.n_bins
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.boac_sysmat_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def pattern(self):
+        nn = self.g.n * self.g.n
+        i32 = dict(dtype=torch.int32, device=self.device)
+        row_ptr, col = torch.empty(self.rows + 1, **i32), torch.empty(self.nnz, **i32)
+        colT_ptr, rowT = torch.empty(nn + 1, **i32), torch.empty(self.nnz, **i32)
+        check("boac_sysmat_pattern", self._lib.boac_sysmat_pattern(
+            self._h, _ptr(row_ptr), _ptr(col), _ptr(colT_ptr), _ptr(rowT), _stream(self.device)))
+        return row_ptr, col, colT_ptr, rowT
+
+    def values(self, mu: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        _need(mu, "mu", torch.float32)
+        B = mu.shape[0]
+        shape = self.vals_shape(B, self.nnz)
+        vals = out if out is not None else torch.empty(shape, dtype=torch.float32, device=mu.device)
+        _need(vals, "vals", torch.float32, shape)
+        check("boac_sysmat_values", self._lib.boac_sysmat_values(self._h, _ptr(mu), B, _ptr(vals),
+                                                                 _stream(mu.device)))
+        return vals
+
+    def project(self, vals: torch.Tensor, F: torch.Tensor) -> torch.Tensor:
+        _need(F, "F", torch.float32)
+        B = F.shape[0]
+        _need(vals, "vals", torch.float32, self.vals_shape(B, self.nnz))
+        q = torch.empty(B, self.g.n_views, self.g.n_bins, dtype=torch.float32, device=F.device)
+        check("boac_sysmat_project", self._lib.boac_sysmat_project(self._h, _ptr(vals), _ptr(F), B, _ptr(q),
+                                                                   _stream(F.device)))
+        return q
+
+    def workspace(self, B: int) -> torch.Tensor:
+        nbytes = int(self._lib.boac_sysmat_mlem_workspace_bytes(self._h, int(B)))
+        return torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+
+    def mlem(self, vals: torch.Tensor, S: torch.Tensor, F: torch.Tensor, K: int, score: bool = True,
+             include_lgamma: bool = True, ws: torch.Tensor | None = None):
+        """K MLEM iterations on F [B, n, n] in place; returns (F, L or None)."""
+        _need(F, "F", torch.float32)
+        B = F.shape[0]
+        _need(vals, "vals", torch.float32, self.vals_shape(B, self.nnz))
+        S, stride = _sino(S, self.g, B)
+        ws = ws if ws is not None else self.workspace(B)
+        L = torch.empty(B, dtype=torch.float64, device=F.device) if score else None
+        check("boac_sysmat_mlem", self._lib.boac_sysmat_mlem(
+            self._h, _ptr(vals), _ptr(S), stride, _ptr(F), int(K), B, _ptr(L), int(include_lgamma),
+            _ptr(ws), ws.numel(), _stream(F.device)))
+        return F, L
+
+
 class BoacScore(torch.autograd.Function):
     """ln P(S | F^K(c), A^mu(c)) as a differentiable function of the Legendre
     coefficients c[B, 6] (tissue values t), or of the 9-parameter model

@@ -70,3 +70,22 @@ def test_host_side_argument_checks(lib):
     assert lib.boac_workspace_bytes(ctypes.byref(good), 1, _lib.OP_PROJECT) == 0
     # per candidate: its attenuation table (60 views) and 15 per-grid partial images
     assert lib.boac_workspace_bytes(ctypes.byref(good), 3, _lib.OP_BACKPROJECT) == 512 + 3 * (60 + 15) * 64 * 64 * 4
+
+
+def test_sysmat_host_side_checks(lib):
+    """The explicit-matrix entry points reject null handles and bad
+    geometries before any CUDA call."""
+    from paper_2109_11920_gb300 import _lib
+    G = _lib.Geom
+    fake = ctypes.c_void_p(0x1000)
+    h = ctypes.c_void_p()
+    assert lib.boac_sysmat_create(ctypes.byref(G(4, 4, 60, 0.4, 0.4)), ctypes.byref(h), None) == _lib.BOAC_EINVAL
+    assert h.value is None
+    assert lib.boac_sysmat_create(ctypes.byref(G.make(64, 0.4, 60)), None, None) == _lib.BOAC_EINVAL
+    assert lib.boac_sysmat_nnz(None) == -1
+    assert lib.boac_sysmat_destroy(None) == _lib.BOAC_EINVAL
+    assert lib.boac_sysmat_mlem_workspace_bytes(None, 4) == 0
+    assert lib.boac_sysmat_values(None, fake, 1, fake, None) == _lib.BOAC_EINVAL
+    assert lib.boac_sysmat_project(None, fake, fake, 1, fake, None) == _lib.BOAC_EINVAL
+    assert lib.boac_sysmat_pattern(None, fake, fake, fake, fake, None) == _lib.BOAC_EINVAL
+    assert lib.boac_sysmat_mlem(None, fake, fake, 0, fake, 5, 1, None, 1, fake, 1 << 20, None) == _lib.BOAC_EINVAL
