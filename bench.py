@@ -579,17 +579,18 @@ def run_workload(args):
     elif name == "sysmat":
         # the batched workload through the explicit system matrix
         wl = synth.BATCHED
+        Bs = args.candidates  # the batched workload's 256 unless given (smaller cases for profiling)
         g, t, (S,) = _phantom_sinograms(boac, Geom, Tissue, dev, wl.n, wl.dx, wl.V, wl.counts, [wl.seed])
-        c = torch.tensor(synth.candidates(synth.streams(wl.seed)[2], wl.B).astype(np.float32), device=dev)
+        c = torch.tensor(synth.candidates(synth.streams(wl.seed)[2], Bs).astype(np.float32), device=dev)
         mu = boac.boac_rasterize_mu(g, t, c)
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         m = boac.SysMat(g, dev)
         torch.cuda.synchronize(dev)
         build_ms = (time.perf_counter() - t0) * 1e3
-        vals = torch.empty(boac.SysMat.vals_shape(wl.B, m.nnz), dtype=torch.float32, device=dev)
-        ws = m.workspace(wl.B)
-        F = torch.ones(wl.B, wl.n, wl.n, device=dev)
+        vals = torch.empty(boac.SysMat.vals_shape(Bs, m.nnz), dtype=torch.float32, device=dev)
+        ws = m.workspace(Bs)
+        F = torch.ones(Bs, wl.n, wl.n, device=dev)
         ms = _timed(lambda: (m.values(mu, out=vals), m.mlem(vals, S, F.fill_(1.0), wl.K, ws=ws)), dev)
         ms_vals = _timed(lambda: m.values(mu, out=vals), dev)
         ms_k0 = _timed(lambda: m.mlem(vals, S, F, 0, ws=ws), dev)  # sensitivity + score
@@ -597,15 +598,15 @@ def run_workload(args):
         peak_gbs, peak_kind = measured_peak_gbs()
         # per iteration the two products stream both value copies of every
         # candidate once (the shared pattern is read once per group of 8)
-        it_bytes = wl.B * 2 * 4 * m.nnz
-        work = [(wl.V, wl.n, wl.K)] * wl.B
+        it_bytes = Bs * 2 * 4 * m.nnz
+        work = [(wl.V, wl.n, wl.K)] * Bs
         extra = {"nnz": m.nnz, "pattern_build_ms": build_ms, "values_ms": ms_vals, "iteration_ms": it_ms,
                  "roofline_hbm": {"kernels": "forward_kernel + backward_update_kernel (one MLEM iteration)",
                                   "achieved": it_bytes / (it_ms / 1e3) / 1e9, "peak": peak_gbs, "unit": "GB/s",
                                   "frac": it_bytes / (it_ms / 1e3) / 1e9 / peak_gbs,
                                   "peak_kind": f"{peak_kind} hbm_gbs (copy)",
                                   "algorithmic_bytes_per_iteration": it_bytes}}
-        desc = (f"{wl.name} through the explicit system matrix: {wl.B} candidates x {wl.K} MLEM iterations, "
+        desc = (f"{wl.name} through the explicit system matrix: {Bs} candidates x {wl.K} MLEM iterations, "
                 f"{wl.n}x{wl.n}, {wl.V} views; value fill + MLEM + score per step")
         m.close()
     elif name in ("grad", "grad_params"):
