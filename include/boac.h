@@ -79,7 +79,8 @@ enum {
     BOAC_OP_MLEM = 2,
     BOAC_OP_MLEM_PLAIN = 3,
     BOAC_OP_SCORE = 4,
-    BOAC_OP_SCORE_GRAD = 5
+    BOAC_OP_SCORE_GRAD = 5,
+    BOAC_OP_MLEM_UNFUSED = 6
 };
 
 /* Human-readable name of a status code (static string, never NULL). */
@@ -168,14 +169,29 @@ int boac_backproject(const boac_geom *g, const float *mu, const float *y,
  * iteration of every candidate on chip (n <= 128: one CTA per candidate;
  * n = 256 with n_views % 4 == 0, and n = 128 with n_views % 4 == 0 when B
  * is too small to give every SM a candidate: a thread-block cluster per
- * candidate, the image split into bands of rows over its CTAs).  The choice
- * depends on B, so query the workspace with the same B.  boac_mlem_plain is the
+ * candidate, the image split into bands of rows over its CTAs); batches
+ * too small to fill the GPU that way (at most 32 candidates at n = 64 and
+ * 96, 16 at 128, 2 at 256, scaled by the SM count / 152) run the unfused
+ * batched kernels of boac_mlem_unfused instead.  The choice depends on B,
+ * so query the workspace with the same B.  boac_mlem_plain is the
  * launch-per-step path: one candidate at a time, separate project / ratio /
  * backproject / update kernels per iteration (the comparison baseline).
  * Workspace: boac_workspace_bytes(g, B, BOAC_OP_MLEM / BOAC_OP_MLEM_PLAIN). */
 int boac_mlem(const boac_geom *g, const float *mu, const float *S,
               long long s_stride, float *F, int K, int B, double *L,
               int include_lgamma, void *ws, size_t ws_bytes, void *stream);
+/* boac_mlem_unfused: the same MLEM over the whole batch with one launch per
+ * step (attenuation table once; per iteration the grouped projector, the
+ * ratio, the grouped back-projection and the update, each covering every
+ * candidate, so one candidate spreads over many CTAs).  Same arguments,
+ * conventions and errors as boac_mlem; workspace boac_workspace_bytes(g, B,
+ * BOAC_OP_MLEM_UNFUSED) (the attenuation tables, 4 n_views n^2 bytes per
+ * candidate, dominate); deterministic; no device waits (the workspace status
+ * word is set to 0). */
+int boac_mlem_unfused(const boac_geom *g, const float *mu, const float *S,
+                      long long s_stride, float *F, int K, int B, double *L,
+                      int include_lgamma, void *ws, size_t ws_bytes,
+                      void *stream);
 int boac_mlem_plain(const boac_geom *g, const float *mu, const float *S,
                     long long s_stride, float *F, int K, int B, double *L,
                     int include_lgamma, void *ws, size_t ws_bytes,

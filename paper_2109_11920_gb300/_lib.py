@@ -31,6 +31,7 @@ OP_MLEM = 2
 OP_MLEM_PLAIN = 3
 OP_SCORE = 4
 OP_SCORE_GRAD = 5
+OP_MLEM_UNFUSED = 6
 
 
 class Geom(ctypes.Structure):
@@ -86,6 +87,7 @@ SIGNATURES = {
     "boac_backproject": (_I, [_GP, _P, _P, _I, _P, _P, _SZ, _P]),
     "boac_mlem": (_I, [_GP, _P, _P, _LL, _P, _I, _I, _P, _I, _P, _SZ, _P]),
     "boac_mlem_plain": (_I, [_GP, _P, _P, _LL, _P, _I, _I, _P, _I, _P, _SZ, _P]),
+    "boac_mlem_unfused": (_I, [_GP, _P, _P, _LL, _P, _I, _I, _P, _I, _P, _SZ, _P]),
     "boac_mlem_noalloc": (_I, [_GP, _P, _P, _LL, _P, _I, _I, _P, _I, _P]),
     "boac_score": (_I, [_GP, _P, _P, _LL, _P, _I, _I, _P, _P, _SZ, _P]),
     "boac_loglik": (_I, [_GP, _P, _P, _LL, _I, _I, _P, _P]),

@@ -126,25 +126,28 @@ def boac_backproject(g: Geom, mu: torch.Tensor, y: torch.Tensor | None,
 
 def boac_mlem(g: Geom, mu: torch.Tensor, S: torch.Tensor, F: torch.Tensor, K: int,
               score: bool = True, include_lgamma: bool = True, plain: bool = False,
-              ws: torch.Tensor | None = None, L: torch.Tensor | None = None):
+              ws: torch.Tensor | None = None, L: torch.Tensor | None = None, unfused: bool = False):
     """K MLEM iterations in place on F[B, n, n]; returns (F, L[B] float64 or None).
 
-    ``plain=False`` runs the batched persistent fused kernel; ``plain=True``
-    the launch-per-step baseline (one candidate at a time)."""
+    By default the library's batched path (the persistent fused kernel, or
+    for small batches the unfused batched kernels); ``unfused=True`` pins the
+    unfused batched path (boac_mlem_unfused); ``plain=True`` the
+    launch-per-step baseline (one candidate at a time)."""
     _need(mu, "mu", torch.float32)
     B = mu.shape[0]
     _need(mu, "mu", torch.float32, (B, g.n, g.n))
     _need(F, "F", torch.float32, (B, g.n, g.n))
     S, stride = _sino(S, g, B)
-    op = _lib.OP_MLEM_PLAIN if plain else _lib.OP_MLEM
+    op = _lib.OP_MLEM_PLAIN if plain else (_lib.OP_MLEM_UNFUSED if unfused else _lib.OP_MLEM)
     if ws is None:
         ws = workspace(g, B, op, mu.device)
     if score and L is None:
         L = torch.empty(B, dtype=torch.float64, device=mu.device)
     if L is not None:
         _need(L, "L", torch.float64, (B,))
-    fn = _lib.load().boac_mlem_plain if plain else _lib.load().boac_mlem
-    check("boac_mlem_plain" if plain else "boac_mlem",
+    name = "boac_mlem_plain" if plain else ("boac_mlem_unfused" if unfused else "boac_mlem")
+    fn = getattr(_lib.load(), name)
+    check(name,
           fn(ctypes.byref(g), _ptr(mu), _ptr(S), stride, _ptr(F), int(K), B,
              _ptr(L) if score else None, int(include_lgamma), _ptr(ws),
              ws.numel() if ws is not None else 0, _stream(mu.device)))

@@ -80,6 +80,7 @@ extern "C" size_t boac_workspace_bytes(const boac_geom* g, int B, int op) {
         case BOAC_OP_MLEM: return fused_workspace_bytes(g, B);
         case BOAC_OP_MLEM_PLAIN: return plain_candidate_bytes(g);
         case BOAC_OP_SCORE: return align256(sizeof(float) * (size_t)B * vb);
+        case BOAC_OP_MLEM_UNFUSED: return unfused_workspace_bytes(g, B);
         default: return 0;
     }
 }

@@ -547,6 +547,26 @@ static int default_config(const boac_geom* g, int B) {
     return single_cta_config(g);
 }
 
+// Batches small enough that the unfused batched kernels (boac_unfused.cu:
+// many CTAs per candidate) finish before the fused kernel's one CTA or one
+// cluster per candidate does.  Measured on GB300 (152 SMs) with K = 20 at
+// 60 / 90 / 120 / 180 views: up to 32 candidates at 64 x 64 and 96 x 96
+// (1.9x / 4.7x at B = 1), 16 at 128 x 128 (2.4x at B = 1), 2 at 256 x 256
+// (1.3x at B = 1); both paths scale with the view count, so the bound is
+// per image size, scaled with the SM count.
+static bool use_unfused(const boac_geom* g, int B) {
+    int cap;
+    switch (g->n) {
+        case 64:
+        case 96: cap = 32; break;
+        case 128: cap = 16; break;
+        case 256: cap = 2; break;
+        default: return false;
+    }
+    const int sms = sm_count();
+    return sms > 0 && (long long)B * 152 <= (long long)cap * sms;
+}
+
 static const FusedVariant* get_variant(const boac_geom* g, int config) {
     const FusedVariant* t = variant_table(g->n);
     if (!t || config < 0 || config >= kConfigs) return nullptr;
@@ -639,6 +659,7 @@ static int variant_holders(const boac_geom* g, const FusedVariant* v, int B) {
 }
 
 size_t fused_workspace_bytes(const boac_geom* g, int B) {
+    if (use_unfused(g, B)) return unfused_workspace_bytes(g, B);
     const FusedVariant* v = get_variant(g, default_config(g, B));
     const int h = v ? variant_holders(g, v, B) : 0;
     return h > 0 ? fused_layout(g, v, h, B).total : 0;
@@ -760,6 +781,8 @@ extern "C" int boac_mlem(const boac_geom* g, const float* mu, const float* S, lo
                          size_t ws_bytes, void* stream) {
     if (!geom_ok(g) || !mu || !S || !F || B < 1 || K < 0 || s_stride < 0) return BOAC_EINVAL;
     if (g->n_views % 2) return BOAC_EINVAL;
+    if (use_unfused(g, B))
+        return mlem_unfused(g, mu, S, s_stride, F, K, B, L, include_lgamma, ws, ws_bytes, as_stream(stream));
     const FusedVariant* v = get_variant(g, default_config(g, B));
     if (!v) return BOAC_EUNSUPPORTED;
     const int slots = variant_holders(g, v, B);

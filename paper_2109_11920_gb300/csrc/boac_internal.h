@@ -35,8 +35,14 @@ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 size_t plain_candidate_bytes(const boac_geom* g);
 size_t backproject_candidate_bytes(const boac_geom* g);
 
-// Fused MLEM: workspace for geometry g and B candidates.
+// boac_mlem: workspace for geometry g and B candidates (the fused kernel's,
+// or the unfused path's for the small batches boac_mlem runs there).
 size_t fused_workspace_bytes(const boac_geom* g, int B);
+
+// Batched unfused MLEM (boac_unfused.cu): workspace and the call itself.
+size_t unfused_workspace_bytes(const boac_geom* g, int B);
+int mlem_unfused(const boac_geom* g, const float* mu, const float* S, long long s_stride, float* F, int K,
+                 int B, double* L, int include_lgamma, void* ws, size_t ws_bytes, cudaStream_t st);
 
 // Entries per candidate of the 9-parameter model (c_0..c_5, mu_b, mu_c, dR).
 constexpr int kParams = 9;

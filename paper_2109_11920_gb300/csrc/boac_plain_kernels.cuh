@@ -27,6 +27,9 @@ __global__ void update_kernel(int count, float* __restrict__ F, const float* __r
                               const float* __restrict__ sens);
 __global__ void loglik_kernel(int nbin, const float* __restrict__ q, const float* __restrict__ S,
                               long long s_stride, int include_lgamma, double* __restrict__ L);
+// r = S / q over B candidates (0 where q <= 0), S rows s_stride apart (boac_grad.cu).
+__global__ void ratio_batched_kernel(int B, int nbin, const float* __restrict__ S, long long s_stride,
+                                     const float* __restrict__ q, float* __restrict__ r);
 
 dim3 ray_grid(const boac_geom* g, int B);
 int grid_1d(long long count, int threads);

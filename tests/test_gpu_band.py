@@ -55,15 +55,19 @@ def test_cluster_kernel_agrees_with_the_one_cta_kernel(cuda):
 
 def test_default_256_path_views_180(cuda):
     """The large-slice geometry (180 views: base views on both sides of 45
-    degrees) through boac_mlem's default, against the oracle."""
+    degrees) on a cluster of 5 CTAs and through boac_mlem's default (for one
+    candidate the unfused kernels), against the oracle."""
     p = make_problem(256, 0.1, 180, 5e5, B=1, seed=45)
     g = Geom.make(p.n, p.dx, p.V)
     mu = torch.tensor(p.mu, dtype=torch.float32, device=cuda)
     S = torch.tensor(p.S, dtype=torch.float32, device=cuda)
     F, L = boac.boac_mlem(g, mu, S, torch.ones(1, 256, 256, device=cuda), 2)
+    batch = ragged_one_class(p, g, 2, cuda)
+    Lc = boac.boac_mlem_ragged(batch, config=[6]).cpu().numpy()
     Fo, Lo, _ = oracle.mlem_batch(p.geom, p.mu, p.S, 2)
-    assert rel_l2(F[0].cpu().numpy(), Fo[0]) < 1e-4
-    assert abs(float(L[0]) - Lo[0]) < 1e-6 * abs(Lo[0])
+    for F_run, L_run in ((F[0].cpu().numpy(), float(L[0])), (batch.image(0).cpu().numpy(), float(Lc[0]))):
+        assert rel_l2(F_run, Fo[0]) < 1e-4
+        assert abs(L_run - Lo[0]) < 1e-6 * abs(Lo[0])
 
 
 def test_work_split_over_clusters_and_repeatability(cuda):
@@ -90,16 +94,23 @@ def test_work_split_over_clusters_and_repeatability(cuda):
 
 
 def test_zero_iterations_and_lone_candidate(cuda):
-    """K = 0: the score of the initial image; one candidate on one cluster."""
+    """K = 0: the score of the initial image; one candidate on one cluster
+    (and through boac_mlem's default)."""
     p = make_problem(256, 0.1, 8, 1e5, B=1, seed=49)
     g = Geom.make(p.n, p.dx, p.V)
     mu = torch.tensor(p.mu, dtype=torch.float32, device=cuda)
     S = torch.tensor(p.S, dtype=torch.float32, device=cuda)
     F0 = torch.full((1, 256, 256), 0.5, device=cuda)
+    Lo = oracle.loglik(p.S, oracle.project(p.geom, p.mu[0], np.full((256, 256), 0.5)))
     F, L = boac.boac_mlem(g, mu, S, F0.clone(), 0)
     assert torch.equal(F, F0)
-    Lo = oracle.loglik(p.S, oracle.project(p.geom, p.mu[0], np.full((256, 256), 0.5)))
     assert abs(float(L[0]) - Lo) < 1e-6 * abs(Lo)
+    for cfg in (6, 7, 8):
+        batch = boac.RaggedBatch([g], [0], [0], [mu[0]], [S], device=cuda)
+        batch.F_pool.fill_(0.5)
+        Lc = boac.boac_mlem_ragged(batch, config=[cfg])
+        assert torch.equal(batch.image(0), F0[0]), cfg
+        assert abs(float(Lc[0]) - Lo) < 1e-6 * abs(Lo), cfg
 
 
 def test_largest_view_count(cuda):
@@ -107,11 +118,10 @@ def test_largest_view_count(cuda):
     the largest exponent table per CTA."""
     p = make_problem(256, 0.1, 720, 1e6, B=1, seed=51)
     g = Geom.make(p.n, p.dx, p.V)
-    mu = torch.tensor(p.mu, dtype=torch.float32, device=cuda)
-    S = torch.tensor(p.S, dtype=torch.float32, device=cuda)
-    F, L = boac.boac_mlem(g, mu, S, torch.ones(1, 256, 256, device=cuda), 2)
+    batch = ragged_one_class(p, g, 2, cuda)
+    L = boac.boac_mlem_ragged(batch, config=[6]).cpu().numpy()
     Fo, Lo, _ = oracle.mlem_batch(p.geom, p.mu, p.S, 2)
-    assert rel_l2(F[0].cpu().numpy(), Fo[0]) < 1e-4
+    assert rel_l2(batch.image(0).cpu().numpy(), Fo[0]) < 1e-4
     assert abs(float(L[0]) - Lo[0]) < 1e-6 * abs(Lo[0])
 
 

@@ -83,23 +83,38 @@ def test_adjointness_fp32(cuda, probs, shape):
     assert abs(lhs - rhs) / abs(lhs) < 2e-6
 
 
-def run_mlem(p, dev, K, plain, B=None, S=None):
+def single_cta_config(p):
+    """The one-CTA fused kernel's default shape (4n threads, 8n at 64 x 64)."""
+    return 2 * (1 if p.n == 64 else 2) + (0 if p.V % 4 == 0 else 1)
+
+
+def run_mlem(p, dev, K, plain=False, B=None, S=None, path=None):
+    """path: None / "default" (boac_mlem's choice), "fused" (the persistent
+    fused kernel, pinned through the ragged entry point), "unfused"
+    (boac_mlem_unfused), "plain" (one candidate at a time)."""
+    path = "plain" if plain else (path or "default")
     mu = T(p.mu if B is None else p.mu[:B], dev)
     Bn = mu.shape[0]
-    F = torch.ones(Bn, p.n, p.n, dtype=torch.float32, device=dev)
     S = T(p.S if S is None else S, dev)
-    F, L = boac.boac_mlem(geom(p), mu, S, F, K, score=True, plain=plain)
+    if path == "fused":
+        batch = boac.RaggedBatch([geom(p)], [0] * Bn, [K] * Bn, list(mu), [S] * Bn, device=dev)
+        L = boac.boac_mlem_ragged(batch, config=[single_cta_config(p)])
+        return batch.F_pool.view(Bn, p.n, p.n).cpu().numpy(), L.cpu().numpy()
+    F = torch.ones(Bn, p.n, p.n, dtype=torch.float32, device=dev)
+    F, L = boac.boac_mlem(geom(p), mu, S, F, K, score=True, plain=path == "plain",
+                          unfused=path == "unfused")
     return F.cpu().numpy(), L.cpu().numpy()
 
 
-@pytest.mark.parametrize("plain", [False, True])
-@pytest.mark.parametrize("shape", [SHAPES[0], SHAPES[1]])
-def test_mlem_small(cuda, probs, shape, plain):
-    """20 iterations on the 64 and 96 classes: images within 1e-4, scores
-    (float64 reduction of a float32 projection) within 1e-6 relative."""
+@pytest.mark.parametrize("path", ["default", "fused", "unfused", "plain"])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_mlem_small(cuda, probs, shape, path):
+    """20 iterations on the 64, 96 and 128 classes through every MLEM path:
+    images within 1e-4, scores (float64 reduction of a float32 projection)
+    within 1e-6 relative."""
     p = probs[shape]
     K = 20
-    F, L = run_mlem(p, cuda, K, plain)
+    F, L = run_mlem(p, cuda, K, path=path)
     Fo, Lo, _ = oracle.mlem_batch(p.geom, p.mu, p.S, K)
     for b in range(p.mu.shape[0]):
         assert rel_l2(F[b], Fo[b]) < 1e-4, b
@@ -108,10 +123,16 @@ def test_mlem_small(cuda, probs, shape, plain):
 
 def test_fused_equals_plain(cuda, probs):
     p = probs[SHAPES[2]]
-    F1, L1 = run_mlem(p, cuda, 10, plain=False)
-    F2, L2 = run_mlem(p, cuda, 10, plain=True)
-    assert rel_l2(F1, F2) < 2e-5
-    np.testing.assert_allclose(L1, L2, rtol=1e-7)
+    F1, L1 = run_mlem(p, cuda, 10, path="fused")
+    for path in ("plain", "unfused"):
+        F2, L2 = run_mlem(p, cuda, 10, path=path)
+        assert rel_l2(F1, F2) < 2e-5, path
+        np.testing.assert_allclose(L1, L2, rtol=1e-7, err_msg=path)
+    # the plain and the unfused path run the same kernels in the same order
+    F2, L2 = run_mlem(p, cuda, 10, path="plain")
+    F3, L3 = run_mlem(p, cuda, 10, path="unfused")
+    np.testing.assert_array_equal(F2, F3)
+    np.testing.assert_array_equal(L2, L3)
 
 
 def test_loglik_reduction_given_same_q(cuda, probs):

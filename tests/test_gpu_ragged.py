@@ -16,6 +16,14 @@ pytestmark = pytest.mark.gpu
 CLASSES = [(64, 0.4, 60), (96, 25.6 / 96, 90), (128, 0.2, 120)]
 
 
+def one_candidate(g, mu, S, K, cfg, dev):
+    """The same candidate alone through the ragged entry point at launch
+    configuration cfg: (F, L)."""
+    b1 = boac.RaggedBatch([g], [0], [K], [mu], [S], device=dev)
+    L = boac.boac_mlem_ragged(b1, config=[cfg])
+    return b1.F_pool.view(g.n, g.n), float(L[0])
+
+
 def build(dev, cls, K, seed0=100, counts=2e5):
     """One oracle-built problem per candidate (own phantom, noise, coefficients)."""
     probs = [make_problem(*CLASSES[c], counts=counts, B=1, seed=seed0 + i) for i, c in enumerate(cls)]
@@ -27,17 +35,25 @@ def build(dev, cls, K, seed0=100, counts=2e5):
 
 
 def test_ragged_matches_uniform_and_oracle(cuda):
+    """Mixed classes and iteration counts in one call: at a fixed launch
+    configuration per class every candidate equals its one-candidate call bit
+    for bit; it agrees with boac_mlem's own choice for one candidate (the
+    unfused kernels) to float rounding, and one per class with the oracle."""
     cls = [0, 1, 2, 2, 1, 0, 2, 0, 1, 2, 2, 0]
     K = [2, 5, 3, 6, 4, 3, 2, 6, 2, 4, 5, 1]
     batch, probs = build(cuda, cls, K)
-    L = boac.boac_mlem_ragged(batch).cpu().numpy()
+    config = [2, 5, 4]  # one CTA per candidate: 8n, 4n (two views per grid), 4n threads
+    L = boac.boac_mlem_ragged(batch, config=config).cpu().numpy()
     for b, p in enumerate(probs):
         g = batch.classes[cls[b]]
+        S = torch.tensor(p.S, dtype=torch.float32, device=cuda)
         mu = torch.tensor(p.mu, dtype=torch.float32, device=cuda)
-        F = torch.ones(1, p.n, p.n, device=cuda)
-        F, Lu = boac.boac_mlem(g, mu, torch.tensor(p.S, dtype=torch.float32, device=cuda), F, K[b])
-        torch.testing.assert_close(batch.image(b), F[0], rtol=0, atol=0)
-        assert L[b] == float(Lu[0])
+        F1, L1 = one_candidate(g, mu[0], S, K[b], config[cls[b]], cuda)
+        torch.testing.assert_close(batch.image(b), F1, rtol=0, atol=0)
+        assert L[b] == L1
+        F, Lu = boac.boac_mlem(g, mu, S, torch.ones(1, p.n, p.n, device=cuda), K[b])
+        assert rel_l2(batch.image(b).cpu().numpy(), F[0].cpu().numpy()) < 1e-5
+        assert abs(L[b] - float(Lu[0])) < 1e-6 * abs(L[b])
     for b in (0, 1, 3):  # one per class vs the oracle
         p = probs[b]
         Fo, Lo, _ = oracle.mlem_batch(p.geom, p.mu, p.S, K[b])
@@ -111,9 +127,9 @@ def test_ragged_full_size_sampled(cuda):
 
 def test_ragged_mixes_one_cta_and_cluster_classes(cuda):
     """A 128 x 128 class (one CTA per candidate) and a 256 x 256 class (a
-    cluster of CTAs per candidate) in one call and one workspace: every
-    candidate equals the uniform entry point bit for bit, and one per class
-    the oracle."""
+    cluster of 5 CTAs per candidate) in one call and one workspace: every
+    candidate equals its one-candidate call at the same configuration bit for
+    bit, boac_mlem to float rounding, and one per class the oracle."""
     classes = [(128, 0.2, 120), (256, 0.1, 16)]
     cls = [1, 0, 1, 0, 0, 1, 1]
     K = [3, 4, 2, 2, 5, 1, 4]
@@ -122,14 +138,18 @@ def test_ragged_mixes_one_cta_and_cluster_classes(cuda):
     mu = [torch.tensor(p.mu[0], dtype=torch.float32, device=cuda) for p in probs]
     S = [torch.tensor(p.S, dtype=torch.float32, device=cuda) for p in probs]
     batch = boac.RaggedBatch(geoms, cls, K, mu, S, device=cuda)
-    L = boac.boac_mlem_ragged(batch).cpu().numpy()
+    config = [4, 6]
+    L = boac.boac_mlem_ragged(batch, config=config).cpu().numpy()
     for b, p in enumerate(probs):
         g = geoms[cls[b]]
+        F1, L1 = one_candidate(g, mu[b], S[b], K[b], config[cls[b]], cuda)
+        torch.testing.assert_close(batch.image(b), F1, rtol=0, atol=0)
+        assert L[b] == L1
         F, Lu = boac.boac_mlem(g, torch.tensor(p.mu, dtype=torch.float32, device=cuda),
                                torch.tensor(p.S, dtype=torch.float32, device=cuda),
                                torch.ones(1, p.n, p.n, device=cuda), K[b])
-        torch.testing.assert_close(batch.image(b), F[0], rtol=0, atol=0)
-        assert L[b] == float(Lu[0])
+        assert rel_l2(batch.image(b).cpu().numpy(), F[0].cpu().numpy()) < 1e-5
+        assert abs(L[b] - float(Lu[0])) < 1e-6 * abs(L[b])
     for b in (1, 0):
         p = probs[b]
         Fo, Lo, _ = oracle.mlem_batch(p.geom, p.mu, p.S, K[b])
