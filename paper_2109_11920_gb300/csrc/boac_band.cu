@@ -711,7 +711,7 @@ __global__ void __launch_bounds__(4 * N, N == 64 ? 4 : (N == 128 && NB > 2) ? 2 
                     const int bin = (vs & 1) ? N - 1 - j : j;
                     const float Sv = __ldg(Sg + (size_t)v * N + bin);
                     if (scoring) {
-                        if (r == 0) lacc += loglik_term(Sv, q, a.include_lgamma);
+                        if (r == 0) lacc += loglik_term(Sv, q, a.include_lgamma && !a.lgS);
                     } else {
                         rr[tid] = q > 0.0f ? dx * (Sv / q) : 0.0f;
                     }
@@ -766,7 +766,7 @@ __global__ void __launch_bounds__(4 * N, N == 64 ? 4 : (N == 128 && NB > 2) ? 2 
             if (r == 0 && tid == 0) {
                 double t = 0.0;
                 for (int wi = 0; wi < NT / 32; ++wi) t += dred[wi];
-                a.L[lidx] = t;
+                a.L[lidx] = a.include_lgamma && a.lgS ? t - *a.lgS : t;
             }
         }
 

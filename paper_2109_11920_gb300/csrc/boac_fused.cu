@@ -35,6 +35,7 @@
 #include "boac_device.cuh"
 #include "boac_fused.h"
 #include "boac_internal.h"
+#include "boac_plain_kernels.cuh"
 
 namespace boac {
 
@@ -358,7 +359,7 @@ __global__ void __launch_bounds__(NT, (fused_min_blocks<N, NT>())) mlem_fused_ke
                     q *= dx;
                     const int v = vi == 0 ? vc1 : vi == 1 ? vc2 : vi == 2 ? vr1 : vr2;
                     const float Sv = __ldg(S + (size_t)v * N + ((vi & 1) ? N - 1 - j : j));
-                    if (scoring) lacc += loglik_term(Sv, q, a.include_lgamma);
+                    if (scoring) lacc += loglik_term(Sv, q, a.include_lgamma && !a.lgS);
                     else rr[vi * N + j] = q > 0.0f ? Sv / q : 0.0f;
                 }
                 __syncthreads();
@@ -408,7 +409,7 @@ __global__ void __launch_bounds__(NT, (fused_min_blocks<N, NT>())) mlem_fused_ke
             if (tid == 0) {
                 double t = 0.0;
                 for (int wi = 0; wi < NT / 32; ++wi) t += dred[wi];
-                a.L[lidx] = t;
+                a.L[lidx] = a.include_lgamma && a.lgS ? t - *a.lgS : t;
             }
         }
 
@@ -682,6 +683,7 @@ static FusedArgs base_args(const boac_geom* g, const float* mu, const float* S, 
     a.F = F;
     a.L = L;
     a.include_lgamma = include_lgamma;
+    a.lgS = nullptr;
     a.B = B;
     a.V = g->n_views;
     a.K = K;
@@ -712,6 +714,9 @@ static int launch_uniform(const boac_geom* g, const FusedVariant* v, int slots, 
     if (cudaMemsetAsync(ws + l.status, 0, sizeof(int), st) != cudaSuccess ||
         cudaMemsetAsync(ws + l.ready, 0, sizeof(int) * (size_t)B, st) != cudaSuccess)
         return launch_status();
+    // one shared sinogram: its ln S! sum once, in the status slot's spare bytes
+    if (L && include_lgamma && s_stride == 0)
+        a.lgS = lgamma_sum(g->n_views * g->n_bins, S, reinterpret_cast<double*>(ws + l.status + 8), st);
     return v->launch(a, grid, st);
 }
 

@@ -24,6 +24,9 @@ struct FusedArgs {
     float* F;
     double* L;
     int include_lgamma;
+    // Uniform batch with one shared sinogram: sum_i lgamma(S_i + 1), computed
+    // once and subtracted from each score (nullptr: the term per bin).
+    const double* lgS;
     int B, V, K;
     float dx;
     // Per-CTA slots, written and read by the same CTA within one launch:

@@ -295,7 +295,7 @@ __global__ void grad_coef_kernel(int n, double dx, double mu_b0, double mu_c0, d
 // ------------------------------------------------------------- workspace
 struct GradLayout {
     size_t mu, tab, abar, sens, sensbar, Fbar, Fnew, zbar, mubar, Fk, ck, Fseg, zseg, qseg, rseg, qK,
-        qbar, rbar, partial, total;
+        qbar, rbar, partial, lg, total;
 };
 
 static GradLayout grad_layout(const boac_geom* g, int B, int K, int ckpt) {
@@ -328,6 +328,7 @@ static GradLayout grad_layout(const boac_geom* g, int B, int K, int ckpt) {
     L.qbar = take(Bs * vb);
     L.rbar = take(Bs * vb);
     L.partial = take(bp_partial_floats(g, B));
+    L.lg = take(2 * kLgammaScratchDoubles);  // the ln S! sum of a shared sinogram
     L.total = off;
     return L;
 }
@@ -403,7 +404,10 @@ static int score_grad_run(const boac_geom* g, const boac_tissue* t, const float*
     }
     // ---- score and d L / d q^K
     project_table(g, B, tab, Fk, dx, qK, st);
-    loglik_kernel<<<B, 256, 0, st>>>((int)vb, qK, S, s_stride, include_lgamma, L);
+    const double* lgS = include_lgamma && s_stride == 0
+                            ? lgamma_sum((int)vb, S, reinterpret_cast<double*>(base + lay.lg), st)
+                            : nullptr;
+    loglik_kernel<<<B, 256, 0, st>>>((int)vb, qK, S, s_stride, include_lgamma, L, lgS);
     if (F_out) cudaMemcpyAsync(F_out, Fk, sizeof(float) * cnt_pix, cudaMemcpyDeviceToDevice, st);
     qbar_final_kernel<<<g1b, 256, 0, st>>>(B, (int)vb, S, s_stride, qK, qbar);
     backproject_table(g, B, tab, qbar, dx, Fbar, 0, partial, st);

@@ -145,9 +145,12 @@ __global__ void update_kernel(int count, float* __restrict__ F, const float* __r
 }
 
 // L[cand] = sum_i S_i ln q_i - q_i [- lgamma(S_i + 1)] in float64.  Fixed
-// per-thread strides and a fixed reduction tree: deterministic.
+// per-thread strides and a fixed reduction tree: deterministic.  With lgS
+// (candidates sharing one sinogram) the ln S! term is its precomputed sum,
+// subtracted once, instead of a term per bin.
 __global__ void loglik_kernel(int nbin, const float* __restrict__ q, const float* __restrict__ S,
-                              long long s_stride, int include_lgamma, double* __restrict__ L) {
+                              long long s_stride, int include_lgamma, double* __restrict__ L,
+                              const double* __restrict__ lgS) {
     __shared__ double part[32];
     const int cand = blockIdx.x;
     const float* qc = q + (size_t)cand * nbin;
@@ -158,7 +161,7 @@ __global__ void loglik_kernel(int nbin, const float* __restrict__ q, const float
         double term;
         if (s > 0.0) term = qi > 0.0 ? s * log(qi) - qi : -INFINITY;
         else term = -qi;
-        if (include_lgamma) term -= lgamma(s + 1.0);
+        if (include_lgamma && !lgS) term -= lgamma(s + 1.0);
         acc += term;
     }
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
@@ -167,8 +170,42 @@ __global__ void loglik_kernel(int nbin, const float* __restrict__ q, const float
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
-        L[cand] = t;
+        L[cand] = include_lgamma && lgS ? t - *lgS : t;
     }
+}
+
+// sum_i lgamma(S_i + 1) over one sinogram (the ln S! term of Eq. 5, equal
+// for every candidate that shares the sinogram), float64: block b adds bins
+// b * blockDim + t, b * blockDim + t + G blockDim, ... into part[b] with a
+// fixed reduction tree; one thread then adds part[0..G) in order.
+__global__ void lgamma_partial_kernel(int nbin, const float* __restrict__ S, double* __restrict__ part) {
+    __shared__ double red[32];
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nbin; i += gridDim.x * blockDim.x)
+        acc += lgamma((double)__ldg(S + i) + 1.0);
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        part[blockIdx.x] = t;
+    }
+}
+
+__global__ void lgamma_final_kernel(int nparts, const double* __restrict__ part, double* __restrict__ out) {
+    double t = 0.0;
+    for (int i = 0; i < nparts; ++i) t += part[i];
+    *out = t;
+}
+
+const double* lgamma_sum(int nbin, const float* S, double* scratch, cudaStream_t st) {
+    int parts = (nbin + 255) / 256;
+    if (parts > kLgammaScratchDoubles - 1) parts = kLgammaScratchDoubles - 1;
+    if (parts < 1) parts = 1;
+    lgamma_partial_kernel<<<parts, 256, 0, st>>>(nbin, S, scratch + 1);
+    lgamma_final_kernel<<<1, 1, 0, st>>>(parts, scratch + 1, scratch);
+    return scratch;
 }
 
 dim3 ray_grid(const boac_geom* g, int B) {
@@ -223,7 +260,7 @@ extern "C" int boac_loglik(const boac_geom* g, const float* q, const float* S, l
                            int B, int include_lgamma, double* L, void* stream) {
     if (!geom_ok(g) || !q || !S || !L || B < 1 || s_stride < 0) return BOAC_EINVAL;
     loglik_kernel<<<B, 256, 0, as_stream(stream)>>>(g->n_views * g->n_bins, q, S, s_stride,
-                                                     include_lgamma, L);
+                                                     include_lgamma, L, nullptr);
     return launch_status();
 }
 
@@ -276,7 +313,7 @@ extern "C" int boac_mlem_plain(const boac_geom* g, const float* mu, const float*
         }
         if (L) {
             project_table(g, 1, tab, F_c, dx, q, st);
-            loglik_kernel<<<1, 256, 0, st>>>((int)vb, q, S_c, 0, include_lgamma, L + cand);
+            loglik_kernel<<<1, 256, 0, st>>>((int)vb, q, S_c, 0, include_lgamma, L + cand, nullptr);
         }
         s = launch_status();
         if (s != BOAC_OK) return s;

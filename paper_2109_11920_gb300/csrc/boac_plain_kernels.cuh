@@ -26,7 +26,12 @@ __global__ void ratio_kernel(int count, const float* __restrict__ S, const float
 __global__ void update_kernel(int count, float* __restrict__ F, const float* __restrict__ bp,
                               const float* __restrict__ sens);
 __global__ void loglik_kernel(int nbin, const float* __restrict__ q, const float* __restrict__ S,
-                              long long s_stride, int include_lgamma, double* __restrict__ L);
+                              long long s_stride, int include_lgamma, double* __restrict__ L,
+                              const double* __restrict__ lgS);
+// sum_i lgamma(S_i + 1) of one sinogram S[nbin] into scratch[0]
+// (scratch: kLgammaScratchDoubles doubles, 8-byte aligned); returns scratch.
+constexpr int kLgammaScratchDoubles = 31;
+const double* lgamma_sum(int nbin, const float* S, double* scratch, cudaStream_t st);
 // r = S / q over B candidates (0 where q <= 0), S rows s_stride apart (boac_grad.cu).
 __global__ void ratio_batched_kernel(int B, int nbin, const float* __restrict__ S, long long s_stride,
                                      const float* __restrict__ q, float* __restrict__ r);

@@ -629,10 +629,11 @@ extern "C" int boac_sysmat_project(const boac_sysmat* m, const float* vals, cons
 }
 
 // Workspace: F and sens interleaved [groups][n*n][8] each, r [groups][R][8]
-// (the final q [B][R] reuses it).
+// (the final q [B][R] reuses it), then the ln S! sum of a shared sinogram.
 extern "C" size_t boac_sysmat_mlem_workspace_bytes(const boac_sysmat* m, int B) {
     if (!m || B < 1) return 0;
-    return sizeof(float) * groups_of(B) * kCandGroup * (2 * (size_t)m->g.n * m->g.n + (size_t)m->R);
+    return sizeof(float) * groups_of(B) * kCandGroup * (2 * (size_t)m->g.n * m->g.n + (size_t)m->R) +
+           sizeof(double) * kLgammaScratchDoubles;
 }
 
 extern "C" int boac_sysmat_mlem(const boac_sysmat* m, const float* vals, const float* S, long long s_stride,
@@ -659,7 +660,9 @@ extern "C" int boac_sysmat_mlem(const boac_sysmat* m, const float* vals, const f
     if (L) {
         forward_kernel<true, false><<<rows_grid(R, B), threads, 0, st>>>(R, nn, m->nnz, m->row_ptr, m->col, vals,
                                                                         Fi, B, S, s_stride, r);
-        loglik_kernel<<<B, 256, 0, st>>>(R, r, S, s_stride, include_lgamma, L);
+        double* scratch = reinterpret_cast<double*>(r + G * (size_t)R * kCandGroup);
+        const double* lgS = include_lgamma && s_stride == 0 ? lgamma_sum(R, S, scratch, st) : nullptr;
+        loglik_kernel<<<B, 256, 0, st>>>(R, r, S, s_stride, include_lgamma, L, lgS);
     }
     return launch_status();
 }

@@ -72,7 +72,11 @@ int mlem_unfused(const boac_geom* g, const float* mu, const float* S, long long 
     if (L) {
         s = project_table(g, B, tab, F, dx, q, st);
         if (s != BOAC_OK) return s;
-        loglik_kernel<<<B, 256, 0, st>>>((int)vb, q, S, s_stride, include_lgamma, L);
+        // one shared sinogram: its ln S! sum once, in the status slot's spare bytes
+        const double* lgS = include_lgamma && s_stride == 0
+                                ? lgamma_sum((int)vb, S, reinterpret_cast<double*>(base + l.status + 8), st)
+                                : nullptr;
+        loglik_kernel<<<B, 256, 0, st>>>((int)vb, q, S, s_stride, include_lgamma, L, lgS);
     }
     return launch_status();
 }
