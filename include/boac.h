@@ -49,7 +49,7 @@ extern "C" {
 #define BOAC_EINVAL (-1)       /* bad shape, null pointer, stride or mode   */
 #define BOAC_ECUDA (-2)        /* a CUDA call or launch failed              */
 #define BOAC_EWORKSPACE (-3)   /* workspace missing or too small            */
-#define BOAC_EUNSUPPORTED (-4) /* valid geometry this build has no kernel for */
+#define BOAC_EUNSUPPORTED (-4) /* valid geometry the library has no kernel for */
 #define BOAC_ETIMEOUT (-5)     /* a bounded wait on the device ran out (see
                                   boac_workspace_status)                   */
 

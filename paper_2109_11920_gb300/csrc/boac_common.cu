@@ -63,7 +63,7 @@ extern "C" const char* boac_status_string(int status) {
         case BOAC_EINVAL: return "invalid argument";
         case BOAC_ECUDA: return "CUDA error";
         case BOAC_EWORKSPACE: return "workspace missing or too small";
-        case BOAC_EUNSUPPORTED: return "geometry not supported by this build";
+        case BOAC_EUNSUPPORTED: return "geometry not supported by the library";
         case BOAC_ETIMEOUT: return "a bounded wait on the device ran out";
         default: return "unknown status";
     }
