@@ -254,9 +254,11 @@ int boac_mlem_ragged(const boac_geom *classes, int n_classes,
  * cannot allocate device memory when they call the library (code running
  * under another framework's allocator or inside a callback where cudaMalloc
  * is not allowed, or a host process without an allocator of its own).
- * Same arguments and results as boac_mlem, minus the workspace: the fused
- * kernel's scratch comes from a 64 MiB array built into the library, which
- * every GPU that loads the library keeps until the process exits.
+ * Same arguments and results as boac_mlem, minus the workspace (always the
+ * one-CTA fused kernel, so results match boac_mlem's to float rounding where
+ * boac_mlem picks another kernel for the batch size): the fused kernel's
+ * scratch comes from a 64 MiB array built into the library, which every GPU
+ * that loads the library keeps until the process exits.
  *   - The first call on a device looks up that array's device address
  *     (cudaGetSymbolAddress); make that first call before any stream capture.
  *   - Fewer candidates run at once when one slot's scratch (about
