@@ -24,7 +24,13 @@ step 3) for a whole batch of candidates at once.  Around it:
   (f_best) at that point and EI is maximised again (Ginsbourger, Le Riche &
   Carraro, "Kriging is well-suited to parallelize optimization", 2010);
 * the stopping rule of step 6: stop when the best EI of a cycle falls below a
-  threshold (or after a cycle budget).
+  threshold (or after a cycle budget);
+* optionally, a gradient polish of the incumbent: the library's exact
+  gradient of the objective (``boac_score_grad``, through the AREA
+  rasterisation) drives L-BFGS-B (Byrd, Lu, Nocedal & Zhu, "A limited memory
+  algorithm for bound constrained optimization", 1995; scipy's
+  implementation) within the search box, so the optimiser uses the
+  gradients alongside its surrogate.
 
 Host-side numpy: the surrogate has at most a few thousand points, so the GPU
 work of a cycle (q candidates x K MLEM iterations) dominates by far.
@@ -158,6 +164,36 @@ class BOResult:
     history_f: np.ndarray
     cycles: int
     ei_trace: list = field(default_factory=list)
+    # gradient polish of the incumbent (None if not run): its start and
+    # result, and the number of objective-and-gradient evaluations
+    polish: dict | None = None
+
+
+def refine_with_gradient(fg, x0, lo, hi, max_iter: int = 30):
+    """Minimise f from x0 within [lo, hi] with L-BFGS-B (scipy), f and its
+    gradient from ``fg(X) -> (f[m], grad[m, dim])`` called on one point at a
+    time.  The search runs in unit-box coordinates (u = (x - lo) / (hi - lo),
+    gradient scaled by hi - lo), so coefficients of different scales weigh
+    alike.  Returns (x, f(x), evaluations)."""
+    from scipy.optimize import minimize
+
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    span = hi - lo
+    calls = [0]
+
+    def fun(u):
+        calls[0] += 1
+        fv, gv = fg(np.asarray(lo + u * span)[None, :])
+        fv, gv = float(np.asarray(fv)[0]), np.asarray(gv, dtype=np.float64)[0] * span
+        if not np.isfinite(fv):
+            return 1e300, np.zeros_like(u)
+        return fv, gv
+
+    u0 = np.clip((np.asarray(x0, dtype=np.float64) - lo) / span, 0.0, 1.0)
+    res = minimize(fun, u0, jac=True, method="L-BFGS-B", bounds=[(0.0, 1.0)] * u0.size,
+                   options={"maxiter": int(max_iter)})
+    return lo + res.x * span, float(res.fun), calls[0]
 
 
 class BOACOptimizer:
@@ -168,8 +204,13 @@ class BOACOptimizer:
     search box is [lo, hi] per coefficient."""
 
     def __init__(self, evaluate, lo, hi, batch: int = 32, init: int = 64, xi: float = 0.01,
-                 ei_threshold: float = 1e-4, max_cycles: int = 20, seed: int = 0):
+                 ei_threshold: float = 1e-4, max_cycles: int = 20, seed: int = 0,
+                 polish=None, polish_iter: int = 30):
+        """``polish``: optional ``fg(X) -> (f, grad)`` of the same objective;
+        after the cycles the incumbent is refined with it (refine_with_gradient)
+        and kept if better."""
         self.evaluate = evaluate
+        self.polish, self.polish_iter = polish, int(polish_iter)
         self.lo = np.asarray(lo, dtype=np.float64)
         self.hi = np.asarray(hi, dtype=np.float64)
         self.batch, self.init, self.xi = int(batch), int(init), float(xi)
@@ -215,14 +256,22 @@ class BOACOptimizer:
             U = np.vstack([U, P])
             f = np.append(f, fp)
         i = int(np.nanargmin(np.where(np.isfinite(f), f, np.inf)))
-        return BOResult(self._from_unit(U[i]), float(f[i]), self._from_unit(U), f, cycles, ei_trace)
+        best_c, best_f = self._from_unit(U[i]), float(f[i])
+        polish = None
+        if self.polish is not None:
+            x, fx, calls = refine_with_gradient(self.polish, best_c, self.lo, self.hi, self.polish_iter)
+            polish = {"start_c": best_c, "start_f": best_f, "c": x, "f": fx, "evaluations": calls}
+            if fx < best_f:
+                best_c, best_f = x, fx
+        return BOResult(best_c, best_f, self._from_unit(U), f, cycles, ei_trace, polish)
 
 
-def gpu_objective(g, t, S, K: int, device=None, include_lgamma: bool = False):
+def gpu_objective(g, t, S, K: int, device=None, include_lgamma: bool = False, mode=None):
     """-ln P(S | F^K(c), A^mu(c)) for a batch of coefficient vectors, on the
-    GPU: rasterise (Eq. 3-4), K fused MLEM iterations, Eq. 5 score.  Rows of
-    6 are Legendre coefficients with the tissue values t; rows of 9 are the
-    9-parameter model (c_0..c_5, mu_b, mu_c, dR) and t is not used."""
+    GPU: rasterise (Eq. 3-4; CENTER unless ``mode`` says otherwise), K MLEM
+    iterations, Eq. 5 score.  Rows of 6 are Legendre coefficients with the
+    tissue values t; rows of 9 are the 9-parameter model (c_0..c_5, mu_b,
+    mu_c, dR) and t is not used."""
     import torch
 
     from . import api
@@ -231,12 +280,36 @@ def gpu_objective(g, t, S, K: int, device=None, include_lgamma: bool = False):
 
     def evaluate(C: np.ndarray) -> np.ndarray:
         c = torch.tensor(np.asarray(C, dtype=np.float32), device=dev)
+        m = api._lib.RASTER_CENTER if mode is None else mode
         if c.shape[1] == 9:
-            mu = api.boac_rasterize_mu_params(g, c)
+            mu = api.boac_rasterize_mu_params(g, c, m)
         else:
-            mu = api.boac_rasterize_mu(g, t, c)
+            mu = api.boac_rasterize_mu(g, t, c, m)
         F = torch.ones(c.shape[0], g.n, g.n, device=dev)
         _, L = api.boac_mlem(g, mu, S, F, K, include_lgamma=include_lgamma)
         return (-L).cpu().numpy()
 
     return evaluate
+
+
+def gpu_objective_and_grad(g, t, S, K: int, ckpt_every: int = 2, device=None,
+                           include_lgamma: bool = False):
+    """The objective of ``gpu_objective(..., mode=RASTER_AREA)`` with its
+    gradient: fg(C) -> (-ln P [m], -d ln P / dc [m, 6 or 9]) from
+    boac_score_grad / boac_score_grad_params (reverse mode through the K MLEM
+    iterations and the AREA rasterisation) for a batch of rows."""
+    import torch
+
+    from . import api
+
+    dev = device or S.device
+
+    def fg(C: np.ndarray):
+        c = torch.tensor(np.asarray(C, dtype=np.float32), device=dev)
+        if c.shape[1] == 9:
+            L, grad, _ = api.boac_score_grad_params(g, c, S, K, ckpt_every, include_lgamma)
+        else:
+            L, grad, _ = api.boac_score_grad(g, t, c, S, K, ckpt_every, include_lgamma)
+        return -L.cpu().numpy(), -grad.cpu().numpy()
+
+    return fg

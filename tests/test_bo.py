@@ -109,3 +109,65 @@ def test_driver_converges_on_a_synthetic_objective():
     calls.clear()
     res2 = bo.BOACOptimizer(evaluate, lo, hi, batch=4, init=16, ei_threshold=1e9, seed=5).run()
     assert res2.cycles == 1 and calls == [16]
+
+
+def test_gradient_polish_known_minima():
+    """refine_with_gradient (L-BFGS-B in unit-box coordinates): an
+    anisotropic quadratic with its minimum inside the box is found from a
+    corner; a minimum outside the box lands on the violated bound with the
+    other coordinates at their optimum; Rosenbrock's valley reaches (1, 1)."""
+    lo, hi = np.array([5.0, -1.0, -0.5]), np.array([10.0, 1.0, 0.5])
+    m = np.array([8.0, 0.3, -0.2])
+    w = np.array([1.0, 50.0, 400.0])
+
+    def fg(X, m=m):
+        X = np.asarray(X, dtype=np.float64)
+        assert np.all(X >= lo - 1e-12) and np.all(X <= hi + 1e-12)
+        return np.sum(w * (X - m) ** 2, axis=1), 2 * w * (X - m)
+
+    x, fx, calls = bo.refine_with_gradient(fg, hi, lo, hi, max_iter=100)
+    np.testing.assert_allclose(x, m, atol=1e-5)
+    assert fx < 1e-8 and calls >= 2
+    m_out = np.array([12.0, 0.3, -0.2])  # c_0 beyond its upper bound
+    x, _, _ = bo.refine_with_gradient(lambda X: fg(X, m_out), lo, lo, hi, max_iter=100)
+    assert x[0] == pytest.approx(hi[0], abs=1e-9)
+    np.testing.assert_allclose(x[1:], m_out[1:], atol=1e-5)
+
+    def rosen(X):
+        x1, x2 = X[:, 0], X[:, 1]
+        f = (1 - x1) ** 2 + 100 * (x2 - x1 ** 2) ** 2
+        g = np.stack([-2 * (1 - x1) - 400 * x1 * (x2 - x1 ** 2), 200 * (x2 - x1 ** 2)], axis=1)
+        return f, g
+
+    x, fx, _ = bo.refine_with_gradient(rosen, np.array([-1.2, 1.0]), np.array([-2.0, -2.0]),
+                                       np.array([2.0, 2.0]), max_iter=500)
+    np.testing.assert_allclose(x, [1.0, 1.0], atol=1e-4)
+
+
+def test_gradient_polish_in_the_driver():
+    """The driver's optional polish starts from the BO incumbent, keeps the
+    better point, and does not run without a gradient function; non-finite
+    values (an infeasible region) do not stop it."""
+    c_star = np.array([8.0, 0.3, -0.6, 0.2, -0.1, 0.05])
+    lo, hi = c_star - 0.5, c_star + 0.5
+    scale = hi - lo
+
+    def evaluate(C):
+        C = np.asarray(C)
+        f = np.sum(((C - c_star) / scale) ** 2, axis=1)
+        return np.where(C[:, 0] > c_star[0] + 0.45, np.inf, f)
+
+    def fg(C):
+        C = np.asarray(C)
+        f = evaluate(C)
+        return f, 2 * (C - c_star) / scale ** 2
+
+    res0 = bo.BOACOptimizer(evaluate, lo, hi, batch=4, init=16, max_cycles=2, ei_threshold=0.0, seed=3).run()
+    assert res0.polish is None
+    res = bo.BOACOptimizer(evaluate, lo, hi, batch=4, init=16, max_cycles=2, ei_threshold=0.0, seed=3,
+                           polish=fg).run()
+    assert res.polish is not None
+    np.testing.assert_array_equal(res.polish["start_c"], res0.best_c)
+    assert res.polish["start_f"] == res0.best_f
+    assert res.best_f <= res0.best_f and res.best_f < 1e-10
+    np.testing.assert_allclose(res.best_c, c_star, atol=1e-5)
