@@ -228,10 +228,31 @@ def run_reference(args, rank, world):
         "data": "synthetic", "config": CONFIG,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle",
                          "sample": f"per step {cores} candidates x {K_ref} MLEM iterations + score "
-                                   f"of the {WL.n}x{WL.n}/{WL.V}-view batch, one candidate per thread"},
+                                   f"of the {WL.n}x{WL.n}/{WL.V}-view batch, one candidate per thread",
+                         "cpu_model": cpu_model()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (/proc/cpuinfo; on Arm the implementer and
+    part codes when no name is given), else the machine type."""
+    import platform
+    fields = {}
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for ln in fh:
+                if ":" in ln:
+                    k, v = ln.split(":", 1)
+                    fields.setdefault(k.strip().lower(), v.strip())
+    except OSError:
+        pass
+    if fields.get("model name"):
+        return fields["model name"]
+    if fields.get("cpu part"):
+        return f"{platform.machine()} (implementer {fields.get('cpu implementer', '?')}, part {fields['cpu part']})"
+    return platform.machine() or "unknown"
 
 
 def cpu_baseline_sample(dev=None):
@@ -248,10 +269,16 @@ def cpu_baseline_sample(dev=None):
     t0 = time.perf_counter()
     Fo, Lo, used = oracle.mlem_batch(p.geom, p.mu, p.S, K, with_score=True, nthreads=cores)
     dt = time.perf_counter() - t0
+    # the same code on one thread: one candidate of the sample
+    t1 = time.perf_counter()
+    oracle.mlem_batch(p.geom, p.mu[:1], p.S, K, with_score=True, nthreads=1)
+    dt1 = time.perf_counter() - t1
     out = {"value": B * K / dt, "unit": UNIT, "cores": used, "kind": "oracle",
            "sample": f"{B} candidates x {K} MLEM iterations + score of the "
                      f"{WL.n}x{WL.n}/{WL.V}-view batch (FP64 C, candidates spread over "
-                     f"{used} threads), {dt:.1f} s wall"}
+                     f"{used} threads), {dt:.1f} s wall",
+           "cpu_model": cpu_model(), "host_threads": cores,
+           "value_1thread": K / dt1, "sample_1thread": f"1 candidate x {K} iterations + score, {dt1:.1f} s"}
     if dev is not None:
         import torch
         from paper_2109_11920_gb300 import Geom
