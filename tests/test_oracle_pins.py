@@ -442,3 +442,29 @@ def test_nine_parameter_gradient_identities():
     Lz, gz, _ = oracle.score_grad_params(g, pzero, S, K)
     assert Ln == Lz and gn[8] == 0.0 and gz[8] == 0.0
     np.testing.assert_array_equal(gn[:8], gz[:8])
+
+
+def test_batch_driver_equals_single_candidate_calls():
+    """The threaded batch driver (the reference of every GPU parity test) is
+    the single-candidate code run per candidate: bit-identical images and
+    scores for any thread count, per-candidate iteration counts, per-candidate
+    sinograms, a given F^0 and with or without the ln S! term."""
+    g, mu, S, _ = small_problem(n=24, V=12, counts=5e4, seed=7)
+    rng = np.random.default_rng(8)
+    B = 5
+    mus = np.stack([mu * s for s in (1.0, 0.5, 1.5, 0.0, 1.2)])
+    Ss = np.stack([S * (1 + b % 2) for b in range(B)])
+    iters = np.array([3, 0, 5, 1, 2])
+    F0 = rng.uniform(0.5, 1.5, (B, g.n, g.n))
+    for nthreads in (1, 3, 8):
+        for lg in (True, False):
+            F, L, used = oracle.mlem_batch(g, mus, Ss, iters, F0=F0, include_lgamma=lg, nthreads=nthreads)
+            assert 1 <= used <= nthreads
+            for b in range(B):
+                Fb = oracle.mlem(g, mus[b], Ss[b], int(iters[b]), F0[b])
+                np.testing.assert_array_equal(F[b], Fb)
+                assert L[b] == oracle.score(g, mus[b], Ss[b], Fb, include_lgamma=lg)
+    # shared sinogram, F^0 = 1, no score
+    F, L, _ = oracle.mlem_batch(g, mus, S, 2, with_score=False, nthreads=2)
+    assert L is None
+    np.testing.assert_array_equal(F[2], oracle.mlem(g, mus[2], S, 2))
