@@ -184,8 +184,9 @@ int boac_mlem(const boac_geom *g, const float *mu, const float *S,
  * step (attenuation table once; per iteration the grouped projector, the
  * ratio, the grouped back-projection and the update, each covering every
  * candidate, so one candidate spreads over many CTAs).  Same arguments,
- * conventions and errors as boac_mlem; workspace boac_workspace_bytes(g, B,
- * BOAC_OP_MLEM_UNFUSED) (the attenuation tables, 4 n_views n^2 bytes per
+ * conventions and errors as boac_mlem, except that any view count is
+ * accepted (boac_mlem needs an even one); workspace boac_workspace_bytes(g,
+ * B, BOAC_OP_MLEM_UNFUSED) (the attenuation tables, 4 n_views n^2 bytes per
  * candidate, dominate); deterministic; no device waits (the workspace status
  * word is set to 0). */
 int boac_mlem_unfused(const boac_geom *g, const float *mu, const float *S,
