@@ -67,3 +67,30 @@ def test_mlem_counts_and_sign(params, K):
         #                     = sum of S over the rays with (A F^k)_i > 0
         qn = oracle.project(g, mu, F)
         assert float(qn.sum()) == pytest.approx(float(S[q_prev > 0].sum()), rel=1e-10)
+
+
+@settings(max_examples=15, deadline=None)
+@given(st.integers(12, 20), st.integers(2, 6), st.integers(0, 3), st.integers(0, 2 ** 31 - 1))
+def test_tissue_value_derivatives(n, V, K, seed):
+    """mu is linear in mu_b and mu_c for a fixed boundary, so L is smooth in
+    them: the 9-parameter reverse-mode derivatives match central differences
+    tightly over random heads, tissue values and data."""
+    rng = np.random.default_rng(seed)
+    dx = 24.0 / n
+    g = oracle.Geometry(n, dx, V)
+    p = np.concatenate([[rng.uniform(5.0, 9.0)], rng.uniform(-0.3, 0.3, 5),
+                        [rng.uniform(0.1, 0.2), rng.uniform(0.2, 0.3), rng.uniform(0.4, 0.8)]])
+    mu_true = oracle.rasterize(n, dx, p[6], p[7], p[8], p[:6], oracle.AREA)
+    S = rng.poisson(oracle.project(g, mu_true, rng.uniform(0.5, 2.0, (n, n))) * 20.0).astype(np.float64)
+    L, grad, _ = oracle.score_grad_params(g, p, S, K)
+
+    def L_at(q):
+        mu = oracle.rasterize(n, dx, q[6], q[7], q[8], q[:6], oracle.AREA)
+        return oracle.score(g, mu, S, oracle.mlem(g, mu, S, K))
+
+    for k in (6, 7):
+        h = 1e-5
+        e = np.zeros(9)
+        e[k] = h
+        fd = (L_at(p + e) - L_at(p - e)) / (2 * h)
+        assert grad[k] == pytest.approx(fd, rel=1e-5, abs=1e-6 * (abs(L) + 1.0))
