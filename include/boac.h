@@ -52,6 +52,10 @@ extern "C" {
 #define BOAC_EUNSUPPORTED (-4) /* valid geometry the library has no kernel for */
 #define BOAC_ETIMEOUT (-5)     /* a bounded wait on the device ran out (see
                                   boac_workspace_status)                   */
+#define BOAC_ENONFINITE (-6)   /* not an error of the call: some candidate's
+                                  Eq. 5 score is -inf because q = 0 on a bin
+                                  with S > 0 (boac_workspace_status; the
+                                  candidate is the one whose L is -inf)     */
 
 /* ---- types ------------------------------------------------------------- */
 /* Scanner geometry (see the discretisation above). */
@@ -90,14 +94,53 @@ const char *boac_status_string(int status);
 int boac_abi_version(void);
 
 /* Device status left in a boac_mlem / boac_mlem_ragged workspace by the last
- * call that used it: BOAC_OK, or BOAC_ETIMEOUT if a kernel gave up one of its
+ * call that used it: BOAC_OK; BOAC_ETIMEOUT if a kernel gave up one of its
  * bounded waits (the affected candidates' scores are NaN and their images
- * unspecified).  The fused kernel splits the batch's iterations evenly over
+ * unspecified; this takes precedence); else BOAC_ENONFINITE if some
+ * candidate's score is -inf (Eq. 5 with q_i = 0 < S_i: the image explains
+ * none of a bin's counts -- a valid result, reported per candidate by its
+ * -inf in L, not a failure).  boac_mlem_plain, boac_score and boac_loglik
+ * keep no status word: there the -inf in L is the only report.  The fused kernel splits the batch's iterations evenly over
  * its CTAs, so a candidate may be continued by a second CTA, which waits for
  * a flag from the first; the schedule leaves that wait a whole candidate's
- * worth of slack, and it gives up after about 8 s.  Synchronous: copies the
+ * worth of slack, and it gives up after a limit set by boac_set_wait_cycles
+ * (default about 2 s).  Synchronous: copies the
  * word to *status after the device work queued before it has finished. */
 int boac_workspace_status(const void *ws, size_t ws_bytes, int *status);
+
+/* Limit, in GPU clock cycles, of the bounded hand-over wait described above
+ * (the second part of a cut candidate waiting for the first part's flag),
+ * for every launch that follows, process-wide.  cycles <= 0 restores the
+ * default, 2^32 (about 2 s at 2 GHz).  Returns the previous limit.  A
+ * shorter limit gives up sooner on a GPU shared with other work, where a
+ * CTA of the launch may wait for an SM; a longer one tolerates more such
+ * delay.  The paper has no counterpart (its GPU code is not published). */
+long long boac_set_wait_cycles(long long cycles);
+
+/* ---- test hook of the bounded hand-over wait ----------------------------
+ * The paper has no counterpart.  Runs the fused MLEM kernel of launch
+ * configuration `config` (the ids of boac_mlem_ragged) on exactly `holders`
+ * CTAs (or clusters), all resident at once (BOAC_EUNSUPPORTED otherwise),
+ * for B candidates of K iterations sharing one sinogram S [n_views][n_bins],
+ * and makes the first part of candidate `withhold` (-1: none) keep its
+ * hand-over flag to itself, so that the CTA running that candidate's second
+ * part waits in vain until the limit of boac_set_wait_cycles runs out.  That
+ * CTA then records BOAC_ETIMEOUT in the workspace status word
+ * (boac_workspace_status), sets the candidate's score to NaN and returns;
+ * every other candidate is computed as by boac_mlem, without the ln S! term.
+ * Pick B, K and holders so that the work split cuts `withhold` (with
+ * cap = max(ceil(B K / holders), K), the candidates whose iterations
+ * [j K, (j+1) K) straddle a multiple of cap).  Nothing faults or hangs: the
+ * wait is bounded and the context stays usable.
+ *   ws  boac_test_mlem_handover_bytes(g, B, K, config, holders) bytes.
+ * Errors: BOAC_EINVAL for bad arguments or a configuration the geometry
+ * does not support; BOAC_EWORKSPACE. */
+size_t boac_test_mlem_handover_bytes(const boac_geom *g, int B, int K,
+                                     int config, int holders);
+int boac_test_mlem_handover(const boac_geom *g, const float *mu,
+                            const float *S, float *F, int K, int B, double *L,
+                            int config, int holders, int withhold, void *ws,
+                            size_t ws_bytes, void *stream);
 
 /* Bytes of device workspace that `op` needs for B candidates of geometry g
  * on the current device (0 if none).  For BOAC_OP_SCORE_GRAD the size also
@@ -260,16 +303,22 @@ int boac_mlem_ragged(const boac_geom *classes, int n_classes,
  * boac_mlem picks another kernel for the batch size): the fused kernel's
  * scratch comes from a 64 MiB array built into the library, which every GPU
  * that loads the library keeps until the process exits.
- *   - The first call on a device looks up that array's device address
- *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - Every call looks up that array's device address on the current device
+ *     (cudaGetSymbolAddress); the first call on a device also loads the
+ *     library's GPU code there, so make that first call before any stream
+ *     capture.
+ *   - L is required (BOAC_EINVAL if NULL): the status word of the bounded
+ *     hand-over wait (see boac_workspace_status) lives in the built-in array,
+ *     so here a candidate whose wait gave up shows only as a NaN in L.
  *   - Fewer candidates run at once when one slot's scratch (about
  *     n_views * n^2 / 2 + n^2 floats, plus three 256 x 257 images at n = 256)
  *     does not fit 64 MiB many times; BOAC_EWORKSPACE if not even one fits
  *     (never for n <= 128; at n = 256 above about 500 views).
  *   - Every call shares the one array: calls that can overlap on the GPU
  *     (different streams, or other threads) race and corrupt each other's
- *     results.  Serialise them.  Nothing needs to start at zero: each call
- *     writes every scratch entry it reads.
+ *     results.  Serialise them.  Each call clears, on its stream, what must
+ *     start at zero (the status word and the hand-over flags) and writes
+ *     every other scratch entry before reading it.
  *   - Allocates nothing: no cudaMalloc, cudaFree or allocating library call. */
 int boac_mlem_noalloc(const boac_geom *g, const float *mu, const float *S,
                       long long s_stride, float *F, int K, int B, double *L,

@@ -21,6 +21,7 @@ BOAC_ECUDA = -2
 BOAC_EWORKSPACE = -3
 BOAC_EUNSUPPORTED = -4
 BOAC_ETIMEOUT = -5
+BOAC_ENONFINITE = -6
 
 RASTER_CENTER = 0
 RASTER_AREA = 1
@@ -81,6 +82,9 @@ SIGNATURES = {
     "boac_abi_version": (_I, []),
     "boac_workspace_status": (_I, [_P, _SZ, ctypes.POINTER(ctypes.c_int)]),
     "boac_workspace_bytes": (_SZ, [_GP, _I, _I]),
+    "boac_set_wait_cycles": (_LL, [_LL]),
+    "boac_test_mlem_handover_bytes": (_SZ, [_GP, _I, _I, _I, _I]),
+    "boac_test_mlem_handover": (_I, [_GP, _P, _P, _P, _I, _I, _P, _I, _I, _I, _P, _SZ, _P]),
     "boac_rasterize_mu": (_I, [_GP, _TP, _P, _I, _I, _P, _P]),
     "boac_rasterize_mu_params": (_I, [_GP, _P, _I, _I, _P, _P]),
     "boac_project": (_I, [_GP, _P, _P, _I, _P, _P]),

@@ -124,15 +124,37 @@ def boac_backproject(g: Geom, mu: torch.Tensor, y: torch.Tensor | None,
     return res
 
 
+def boac_set_wait_cycles(cycles: int) -> int:
+    """Process-wide limit (GPU cycles) of the fused kernels' bounded hand-over
+    wait; ``cycles <= 0`` restores the default.  Returns the previous limit."""
+    return int(_lib.load().boac_set_wait_cycles(int(cycles)))
+
+
+def _raise_on_device_status(fn: str, ws: torch.Tensor | None) -> None:
+    """Raise BoacError if the device status word reports a failure
+    (BOAC_ENONFINITE, a -inf score, is a result, not a failure)."""
+    if ws is not None:
+        st = boac_workspace_status(ws)
+        if st not in (_lib.BOAC_OK, _lib.BOAC_ENONFINITE):
+            raise _lib.BoacError(fn, st)
+
+
 def boac_mlem(g: Geom, mu: torch.Tensor, S: torch.Tensor, F: torch.Tensor, K: int,
               score: bool = True, include_lgamma: bool = True, plain: bool = False,
-              ws: torch.Tensor | None = None, L: torch.Tensor | None = None, unfused: bool = False):
+              ws: torch.Tensor | None = None, L: torch.Tensor | None = None, unfused: bool = False,
+              check_status: bool = True):
     """K MLEM iterations in place on F[B, n, n]; returns (F, L[B] float64 or None).
 
     By default the library's batched path (the persistent fused kernel, or
     for small batches the unfused batched kernels); ``unfused=True`` pins the
     unfused batched path (boac_mlem_unfused); ``plain=True`` the
-    launch-per-step baseline (one candidate at a time)."""
+    launch-per-step baseline (one candidate at a time).
+
+    ``check_status`` (batched paths): wait for the call to finish and raise
+    BoacError if a bounded device wait gave up (BOAC_ETIMEOUT in the
+    workspace status word; those candidates' scores are NaN).  Pass False to
+    keep the call asynchronous (required inside CUDA-graph capture) and read
+    ``boac_workspace_status(ws)`` later."""
     _need(mu, "mu", torch.float32)
     B = mu.shape[0]
     _need(mu, "mu", torch.float32, (B, g.n, g.n))
@@ -151,6 +173,8 @@ def boac_mlem(g: Geom, mu: torch.Tensor, S: torch.Tensor, F: torch.Tensor, K: in
           fn(ctypes.byref(g), _ptr(mu), _ptr(S), stride, _ptr(F), int(K), B,
              _ptr(L) if score else None, int(include_lgamma), _ptr(ws),
              ws.numel() if ws is not None else 0, _stream(mu.device)))
+    if check_status and not plain:
+        _raise_on_device_status(name, ws)
     return F, (L if score else None)
 
 
@@ -437,6 +461,11 @@ class RaggedBatch:
         self.ws, self.config = ws, config
         return ws
 
+    def status(self) -> int:
+        """Device status word of the last run (synchronous): BOAC_OK, or
+        BOAC_ETIMEOUT if a bounded hand-over wait gave up."""
+        return boac_workspace_status(self.ws)
+
     def run(self, include_lgamma: bool = True) -> torch.Tensor:
         """Launch the per-class fused kernels (capturable in a CUDA graph)."""
         c = self._config(self.config)
@@ -448,9 +477,12 @@ class RaggedBatch:
 
 
 def boac_mlem_ragged(batch: RaggedBatch, include_lgamma: bool = True, config=None) -> torch.Tensor:
-    """One-shot ragged MLEM + score: returns L[B] (float64); images in batch.F_pool."""
+    """One-shot ragged MLEM + score: returns L[B] (float64); images in batch.F_pool.
+    Waits for the launch and raises BoacError if a bounded device wait gave up."""
     batch.prepare(config)
-    return batch.run(include_lgamma)
+    L = batch.run(include_lgamma)
+    _raise_on_device_status("boac_mlem_ragged", batch.ws)
+    return L
 
 
 # ---------------------------------------------------------------- graphs
@@ -484,9 +516,33 @@ class BatchedEvaluator:
         boac_rasterize_mu(self.g, self.t, self.c, self.mode, out=self.mu)
         self.F.fill_(1.0)
         boac_mlem(self.g, self.mu, self.S, self.F, self.K, score=True, include_lgamma=self.lg,
-                  ws=self.ws, L=self.L)
+                  ws=self.ws, L=self.L, check_status=False)
+
+    def status(self) -> int:
+        """Device status word of the last replay (synchronous)."""
+        return boac_workspace_status(self.ws) if self.ws is not None else _lib.BOAC_OK
 
     def evaluate(self, c: torch.Tensor) -> torch.Tensor:
         self.c.copy_(c, non_blocking=True)
         self.graph.replay()
         return self.L
+
+
+def boac_test_mlem_handover(g: Geom, mu: torch.Tensor, S: torch.Tensor, K: int, config: int, holders: int,
+                            withhold: int):
+    """Test hook of the bounded hand-over wait (boac_test_mlem_handover):
+    returns (F[B, n, n], L[B], device status word, workspace)."""
+    _need(mu, "mu", torch.float32)
+    B = mu.shape[0]
+    _need(S, "S", torch.float32, (g.n_views, g.n_bins))
+    lib = _lib.load()
+    nbytes = int(lib.boac_test_mlem_handover_bytes(ctypes.byref(g), B, int(K), int(config), int(holders)))
+    if nbytes == 0:
+        raise ValueError("invalid arguments for boac_test_mlem_handover")
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=mu.device)
+    F = torch.ones(B, g.n, g.n, dtype=torch.float32, device=mu.device)
+    L = torch.empty(B, dtype=torch.float64, device=mu.device)
+    check("boac_test_mlem_handover", lib.boac_test_mlem_handover(
+        ctypes.byref(g), _ptr(mu), _ptr(S), _ptr(F), int(K), B, _ptr(L), int(config), int(holders),
+        int(withhold), _ptr(ws), ws.numel(), _stream(mu.device)))
+    return F, L, boac_workspace_status(ws), ws

@@ -585,7 +585,7 @@ __global__ void __launch_bounds__(4 * N, N == 64 ? 4 : (N == 128 && NB > 2) ? 2 
                     int f;
                     asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(f) : "l"(a.ready + cand) : "memory");
                     if (f) break;
-                    if (clock64() - t0 > kReadySpinCycles) {
+                    if (clock64() - t0 > a.wait_cycles) {
                         ok = 0;
                         atomicExch(a.status, BOAC_ETIMEOUT);
                         break;
@@ -767,6 +767,7 @@ __global__ void __launch_bounds__(4 * N, N == 64 ? 4 : (N == 128 && NB > 2) ? 2 
                 double t = 0.0;
                 for (int wi = 0; wi < NT / 32; ++wi) t += dred[wi];
                 a.L[lidx] = a.include_lgamma && a.lgS ? t - *a.lgS : t;
+                if (t == -INFINITY) atomicCAS(a.status, BOAC_OK, BOAC_ENONFINITE);
             }
         }
 
@@ -774,7 +775,7 @@ __global__ void __launch_bounds__(4 * N, N == 64 ? 4 : (N == 128 && NB > 2) ? 2 
         for (int i = tid; i < rows * N; i += NT) Fc[(size_t)R0 * N + i] = Fb[(i / N + 1) * P + (i % N) + 1];
         __threadfence();
         cl.sync();  // F written by every band; no CTA still reads another's shared memory
-        if (!last && r == 0 && tid == 0)
+        if (!last && r == 0 && tid == 0 && cand != a.withhold)
             asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(a.ready + cand), "r"(1) : "memory");
     }
 }

@@ -65,6 +65,7 @@ extern "C" const char* boac_status_string(int status) {
         case BOAC_EWORKSPACE: return "workspace missing or too small";
         case BOAC_EUNSUPPORTED: return "geometry not supported by the library";
         case BOAC_ETIMEOUT: return "a bounded wait on the device ran out";
+        case BOAC_ENONFINITE: return "a score is -inf (zero expected counts on a bin with counts)";
         default: return "unknown status";
     }
 }

@@ -30,6 +30,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <atomic>
 #include <vector>
 
 #include "boac_device.cuh"
@@ -267,7 +268,7 @@ __global__ void __launch_bounds__(NT, (fused_min_blocks<N, NT>())) mlem_fused_ke
                     int f;
                     asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(f) : "l"(a.ready + cand) : "memory");
                     if (f) break;
-                    if (clock64() - t0 > kReadySpinCycles) {
+                    if (clock64() - t0 > a.wait_cycles) {
                         ok = 0;
                         atomicExch(a.status, BOAC_ETIMEOUT);
                         break;
@@ -410,13 +411,14 @@ __global__ void __launch_bounds__(NT, (fused_min_blocks<N, NT>())) mlem_fused_ke
                 double t = 0.0;
                 for (int wi = 0; wi < NT / 32; ++wi) t += dred[wi];
                 a.L[lidx] = a.include_lgamma && a.lgS ? t - *a.lgS : t;
+                if (t == -INFINITY) atomicCAS(a.status, BOAC_OK, BOAC_ENONFINITE);
             }
         }
 
         // ---- F out (F^K, or the state handed to the candidate's second part)
         for (int i = tid; i < NN; i += NT) Fc[i] = img0[(i / N + 1) * P + (i % N) + 1];
         __syncthreads();
-        if (!last && tid == 0) {
+        if (!last && tid == 0 && cand != a.withhold) {
             __threadfence();
             asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(a.ready + cand), "r"(1) : "memory");
         }
@@ -698,8 +700,13 @@ static FusedArgs base_args(const boac_geom* g, const float* mu, const float* S, 
     a.status = reinterpret_cast<int*>(ws + l.status);
     a.geo = reinterpret_cast<const int*>(ws + l.geo);
     a.geo_bad = reinterpret_cast<int*>(ws + l.img);
+    a.wait_cycles = wait_cycles();
+    a.withhold = -1;
     return a;
 }
+
+static std::atomic<long long> g_wait_cycles{kWaitCycles};
+long long wait_cycles() { return g_wait_cycles.load(std::memory_order_relaxed); }
 
 // Uniform batch: zero the status and ready flags, then launch the CTAs that
 // have work under the split.
@@ -795,6 +802,52 @@ extern "C" int boac_mlem(const boac_geom* g, const float* mu, const float* S, lo
     if (!ws || ws_bytes < fused_layout(g, v, slots, B).total) return BOAC_EWORKSPACE;
     return launch_uniform(g, v, slots, mu, S, s_stride, F, K, B, L, include_lgamma,
                           static_cast<char*>(ws), as_stream(stream));
+}
+
+extern "C" long long boac_set_wait_cycles(long long cycles) {
+    return g_wait_cycles.exchange(cycles > 0 ? cycles : kWaitCycles);
+}
+
+// Test hook of the bounded hand-over wait: the fused kernel of launch
+// configuration `config` on exactly `holders` CTAs (or clusters), with the
+// first part of candidate `withhold` keeping its flag to itself.
+static int handover_plan(const boac_geom* g, int B, int K, int config, int holders, int withhold,
+                         const FusedVariant** v, FusedLayout* l) {
+    if (!geom_ok(g) || B < 1 || K < 0 || holders < 1 || holders > B || withhold < -1 || withhold >= B)
+        return BOAC_EINVAL;
+    *v = get_variant(g, config);
+    if (!*v) return BOAC_EINVAL;
+    if (variant_holders(g, *v, B) < holders) return BOAC_EUNSUPPORTED;  // must all be resident
+    *l = fused_layout(g, *v, holders, B);
+    return BOAC_OK;
+}
+
+extern "C" size_t boac_test_mlem_handover_bytes(const boac_geom* g, int B, int K, int config, int holders) {
+    const FusedVariant* v;
+    FusedLayout l;
+    return handover_plan(g, B, K, config, holders, -1, &v, &l) == BOAC_OK ? l.total : 0;
+}
+
+extern "C" int boac_test_mlem_handover(const boac_geom* g, const float* mu, const float* S, float* F, int K,
+                                       int B, double* L, int config, int holders, int withhold, void* ws,
+                                       size_t ws_bytes, void* stream) {
+    if (!mu || !S || !F || !L) return BOAC_EINVAL;
+    const FusedVariant* v;
+    FusedLayout l;
+    const int s = handover_plan(g, B, K, config, holders, withhold, &v, &l);
+    if (s != BOAC_OK) return s;
+    if (!ws || ws_bytes < l.total) return BOAC_EWORKSPACE;
+    char* base = static_cast<char*>(ws);
+    cudaStream_t st = as_stream(stream);
+    FusedArgs a = base_args(g, mu, S, 0, F, K, B, L, 0, base, l);
+    a.withhold = withhold;
+    const long long per = K > 0 ? K : 1, units = (long long)B * per;
+    a.cap = split_cap(units, per, holders);
+    const int grid = (int)((units + a.cap - 1) / a.cap);
+    if (cudaMemsetAsync(base + l.status, 0, sizeof(int), st) != cudaSuccess ||
+        cudaMemsetAsync(base + l.ready, 0, sizeof(int) * (size_t)B, st) != cudaSuccess)
+        return launch_status();
+    return v->launch(a, grid, st);
 }
 
 extern "C" int boac_workspace_status(const void* ws, size_t ws_bytes, int* status) {
@@ -911,26 +964,20 @@ namespace boac {
 constexpr size_t kNoAllocScratchBytes = size_t(64) << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-// Device address of g_noalloc_scratch, looked up once per device.  In host
-// code the array's name stands for a host-side shadow, not device memory,
-// so the kernel must be given the address cudaGetSymbolAddress returns.
+// Device address of g_noalloc_scratch on the current device, looked up on
+// every call: in host code the array's name stands for a host-side shadow,
+// not device memory, so the kernel must be given the address
+// cudaGetSymbolAddress returns.  Not caching it keeps the address right after
+// a device reset or a re-created primary context (the module, and the array
+// with it, may then sit elsewhere) and leaves no shared state between host
+// threads; the lookup costs next to nothing beside an MLEM launch.
 static void* noalloc_scratch_ptr() {
-    constexpr int kDev = 64;
-    static void* cached[kDev];
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kDev) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
         cudaGetLastError();
         return nullptr;
     }
-    if (!cached[dev]) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
-            cudaGetLastError();
-            return nullptr;
-        }
-        cached[dev] = p;
-    }
-    return cached[dev];
+    return p;
 }
 
 // Largest number of resident CTA slots whose tables, sensitivity images and
@@ -947,7 +994,10 @@ static int noalloc_slots(const boac_geom* g, const FusedVariant* v, int B) {
 extern "C" int boac_mlem_noalloc(const boac_geom* g, const float* mu, const float* S,
                                  long long s_stride, float* F, int K, int B, double* L,
                                  int include_lgamma, void* stream) {
-    if (!geom_ok(g) || !mu || !S || !F || B < 1 || K < 0 || s_stride < 0) return BOAC_EINVAL;
+    // L is required: the status word of the bounded hand-over wait lives in
+    // the built-in array, out of the caller's reach, so a candidate that gave
+    // up shows only as a NaN score.
+    if (!geom_ok(g) || !mu || !S || !F || !L || B < 1 || K < 0 || s_stride < 0) return BOAC_EINVAL;
     if (g->n_views % 2) return BOAC_EINVAL;
     // the one-CTA kernel: its per-CTA scratch is the smallest
     const FusedVariant* v = get_variant(g, single_cta_config(g));

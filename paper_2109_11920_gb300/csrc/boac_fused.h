@@ -54,16 +54,24 @@ struct FusedArgs {
     long long cap;
     int* ready;    // [B] zeroed before the launch
     int* status;   // 0, or BOAC_ETIMEOUT if a bounded wait ran out
+    // Cycles the second part of a cut candidate waits for the first part's
+    // flag before giving up (boac_set_wait_cycles; default kWaitCycles).
+    long long wait_cycles;
+    // Candidate whose first part does not release its flag (-1: none).  Set
+    // only by boac_test_mlem_handover, to make the bounded wait run out.
+    int withhold;
     // Cluster kernel only: the ray-run records of every (band, grid), and a
     // flag the record kernel sets if a run exceeds the kernel's buffers.
     const int* geo;
     int* geo_bad;
 };
 
-// Cycles a CTA waits for the first part of a cut candidate before giving up
-// (about 8 s at 2 GHz; the schedule leaves it a whole candidate's worth of
-// slack, so the wait ends immediately in practice).
-constexpr long long kReadySpinCycles = 1LL << 34;
+// Default number of cycles a CTA waits for the first part of a cut candidate
+// before giving up (about 2 s at 2 GHz; the schedule leaves the wait a whole
+// candidate's worth of slack, so it ends immediately in practice).
+constexpr long long kWaitCycles = 1LL << 32;
+// The process-wide wait limit in force (boac_set_wait_cycles).
+long long wait_cycles();
 
 // 2^x with the hardware approximation (relative error about 2^-22).
 __device__ __forceinline__ float ex2(float x) {

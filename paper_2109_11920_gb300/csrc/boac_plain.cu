@@ -150,7 +150,7 @@ __global__ void update_kernel(int count, float* __restrict__ F, const float* __r
 // subtracted once, instead of a term per bin.
 __global__ void loglik_kernel(int nbin, const float* __restrict__ q, const float* __restrict__ S,
                               long long s_stride, int include_lgamma, double* __restrict__ L,
-                              const double* __restrict__ lgS) {
+                              const double* __restrict__ lgS, int* status) {
     __shared__ double part[32];
     const int cand = blockIdx.x;
     const float* qc = q + (size_t)cand * nbin;
@@ -171,6 +171,7 @@ __global__ void loglik_kernel(int nbin, const float* __restrict__ q, const float
         double t = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
         L[cand] = include_lgamma && lgS ? t - *lgS : t;
+        if (status && t == -INFINITY) atomicCAS(status, BOAC_OK, BOAC_ENONFINITE);
     }
 }
 

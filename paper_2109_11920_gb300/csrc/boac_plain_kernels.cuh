@@ -25,9 +25,11 @@ __global__ void ratio_kernel(int count, const float* __restrict__ S, const float
                              float* __restrict__ r);
 __global__ void update_kernel(int count, float* __restrict__ F, const float* __restrict__ bp,
                               const float* __restrict__ sens);
+// status (nullable): set to BOAC_ENONFINITE (unless already non-zero) when
+// a candidate's score is -inf (q = 0 on a bin with S > 0).
 __global__ void loglik_kernel(int nbin, const float* __restrict__ q, const float* __restrict__ S,
                               long long s_stride, int include_lgamma, double* __restrict__ L,
-                              const double* __restrict__ lgS);
+                              const double* __restrict__ lgS, int* status = nullptr);
 // sum_i lgamma(S_i + 1) of one sinogram S[nbin] into scratch[0]
 // (scratch: kLgammaScratchDoubles doubles, 8-byte aligned); returns scratch.
 constexpr int kLgammaScratchDoubles = 31;

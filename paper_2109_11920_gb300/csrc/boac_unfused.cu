@@ -76,7 +76,8 @@ int mlem_unfused(const boac_geom* g, const float* mu, const float* S, long long 
         const double* lgS = include_lgamma && s_stride == 0
                                 ? lgamma_sum((int)vb, S, reinterpret_cast<double*>(base + l.status + 8), st)
                                 : nullptr;
-        loglik_kernel<<<B, 256, 0, st>>>((int)vb, q, S, s_stride, include_lgamma, L, lgS);
+        loglik_kernel<<<B, 256, 0, st>>>((int)vb, q, S, s_stride, include_lgamma, L, lgS,
+                                         reinterpret_cast<int*>(base + l.status));
     }
     return launch_status();
 }

@@ -50,6 +50,36 @@ def make_problem(n: int, dx: float, V: int, counts: float, B: int, seed: int = 0
     return Problem(n, dx, V, tissue, mu_true, F_true, S, coefs, mu)
 
 
+def center_tie_mask(n: int, dx: float, coef, dR: float, tol: float = 1e-9) -> np.ndarray:
+    """Pixels whose centre lies within ``tol`` cm of a class boundary of Eq. 4
+    (r = R(theta) or r = R(theta) + dR, R clamped at 0), computed here in
+    float64 with numpy's Legendre series -- independently of the oracle and
+    of the CUDA path.  Only at these pixels may two correct float64
+    evaluations of R (different polynomial recursions) pick different
+    classes."""
+    c = (n - 1) / 2.0
+    jj, ii = np.meshgrid(np.arange(n, dtype=np.float64), np.arange(n, dtype=np.float64))
+    x, y = (jj - c) * dx, (ii - c) * dx
+    r = np.hypot(x, y)
+    z = np.where(r > 0, x / np.where(r > 0, r, 1.0), 1.0)
+    R = np.maximum(np.polynomial.legendre.legval(z, np.asarray(coef, dtype=np.float64)), 0.0)
+    return (np.abs(r - R) < tol) | (np.abs(r - (R + max(dR, 0.0))) < tol)
+
+
+def assert_center_classes(mu, ref, n, dx, coef, dR, tol=1e-9):
+    """CENTER-mode rasterisation (Eq. 4) is a class decision: the CUDA map
+    must equal the oracle's bit for bit at every pixel that is not a tie
+    (``center_tie_mask``)."""
+    mu = np.asarray(mu)
+    ref32 = np.asarray(ref).astype(F32)
+    differ = mu != ref32
+    ties = center_tie_mask(n, dx, coef, dR, tol)
+    bad = differ & ~ties
+    assert not bad.any(), (f"{int(bad.sum())} pixels differ away from a boundary, first at "
+                           f"{np.argwhere(bad)[:3].tolist()}")
+    return int(differ.sum()), int(ties.sum())
+
+
 def rel_l2(a, b) -> float:
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)

@@ -39,6 +39,8 @@ def test_status_strings(lib):
     assert _lib.status_string(0) == "ok"
     assert "invalid" in _lib.status_string(_lib.BOAC_EINVAL)
     assert "workspace" in _lib.status_string(_lib.BOAC_EWORKSPACE)
+    assert "-inf" in _lib.status_string(_lib.BOAC_ENONFINITE)
+    assert "wait" in _lib.status_string(_lib.BOAC_ETIMEOUT)
     assert lib.boac_abi_version() >= 1
 
 

@@ -97,6 +97,33 @@ def test_rasterize_legendre_boundary_against_numpy():
     assert (mu == MU_B).sum() > 100 and (mu == MU_C).sum() > 20
 
 
+
+@pytest.mark.parametrize("coef, dR", [(synth.C_TRUE, DR), ([0.5, 3.0, 0, 0, 0, 0], DR),
+                                      ([-2.0, 0.3, -0.6, 0.2, -0.1, 0.05], DR),
+                                      ([20.0, 0, 0, 0, 0, 0], 0.0)])
+def test_center_class_check_is_exact_away_from_ties(coef, dR):
+    """The CENTER-mode parity check used against the CUDA rasteriser: the
+    oracle's map passes it, few pixels are ties, and one pixel flipped to
+    another class away from a boundary -- or a boundary shifted by a tenth of
+    a pixel -- fails it."""
+    from problems import assert_center_classes, center_tie_mask
+    n, dx = 64, 0.4
+    c = np.asarray(coef, dtype=np.float64)
+    mu = oracle.rasterize(n, dx, MU_B, MU_C, dR, c, oracle.CENTER)
+    assert assert_center_classes(mu.astype(np.float32), mu, n, dx, c, dR)[0] == 0
+    ties = center_tie_mask(n, dx, c, dR)
+    assert ties.sum() <= 2
+    bad = mu.astype(np.float32)
+    i, j = np.argwhere(~ties)[n * n // 2 + 3]
+    bad[i, j] = np.float32(MU_C if mu[i, j] != MU_C else MU_B)
+    with pytest.raises(AssertionError):
+        assert_center_classes(bad, mu, n, dx, c, dR)
+    if c[0] > 0 and c[0] < 10:
+        shifted = oracle.rasterize(n, dx, MU_B, MU_C, dR, c + np.array([0.04, 0, 0, 0, 0, 0]),
+                                   oracle.CENTER)
+        with pytest.raises(AssertionError):
+            assert_center_classes(shifted.astype(np.float32), mu, n, dx, c, dR)
+
 def test_rasterize_area_mode():
     """AREA mode: equals CENTER more than a pixel from any boundary, and its
     integral approaches the exact annulus areas (error O(dx^2) per unit
@@ -195,6 +222,26 @@ def test_exact_rotations_quarter_turns():
         ref = dx * (att * Fr).sum(axis=0)
         np.testing.assert_allclose(q[v], ref, rtol=1e-13, atol=1e-15)
 
+
+
+def test_attenuation_table_quarter_turns():
+    """The public attenuation-factor table (Eq. 1 inner integral) at
+    phi = 0, 90, 180, 270 deg: sample (k, b) of view v is pixel (k, b) of
+    the image turned v quarter turns, so every factor is
+    exp(-dx (mu_k / 2 + sum_{k' > k} mu_k')) with the sum a numpy cumsum
+    along the column towards the detector (k = n - 1)."""
+    n, dx = 18, 0.6
+    rng = np.random.default_rng(31)
+    mu = rng.uniform(0, 0.4, (n, n))
+    g = oracle.Geometry(n, dx, 4)
+    a = oracle.attenuation(g, mu)
+    assert a.shape == (4, n, n)
+    for v in range(4):
+        mr = np.rot90(mu, k=v)
+        suffix = np.cumsum(mr[::-1], axis=0)[::-1] - mr
+        np.testing.assert_allclose(a[v], np.exp(-dx * (0.5 * mr + suffix)), rtol=1e-14, atol=0)
+    # mu = 0: no attenuation anywhere
+    np.testing.assert_array_equal(oracle.attenuation(g, np.zeros((n, n))), np.ones((4, n, n)))
 
 # ----------------------------------------------------------------- Eq. 2
 def test_adjointness():

@@ -4,9 +4,10 @@ callback where cudaMalloc is not allowed).  It takes its scratch from an
 array built into the library instead of a caller workspace.
 
 Called here through the raw C ABI (ctypes, device pointers) and checked
-against boac_mlem, the workspace-taking entry point, on two calls in a row
-with different inputs, so that leftovers of the first call in the shared
-scratch would show up in the second.  This file is named to be collected
+against boac_mlem, the workspace-taking entry point, and against the FP64
+oracle on sampled candidates, on two calls in a row with different inputs,
+so that leftovers of the first call in the shared scratch would show up in
+the second.  This file is named to be collected
 last; it passes on its own in a fresh process and after the other tests.
 """
 import ctypes
@@ -15,6 +16,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_2109_11920_gb300 import Geom, _lib
 from paper_2109_11920_gb300 import api as boac
 from problems import make_problem, rel_l2
@@ -35,9 +37,16 @@ def test_noalloc_matches_workspace_entry_point(cuda):
     from paper_2109_11920_gb300 import build
     build.build()
     lib = _lib.load()
-    # 128 x 128, 120 views: one slot needs ~7.9 MB of scratch, so the 64 MiB
-    # array holds 8 slots and 20 candidates take several rounds per CTA.
-    p = make_problem(128, 0.2, 120, 1e6, B=20, seed=5)
+    # 128 x 128, 120 views: one CTA slot's scratch is its attenuation
+    # exponents, V/2 (n^2 + n) floats, and its sensitivity image, n^2 floats
+    # (about 4.0 MB), so the 64 MiB array holds 16 slots.  20 candidates are
+    # more than that: the work split then cuts candidates between two CTAs
+    # (the hand-over path) and every slot is reused within a call.
+    n, V = 128, 120
+    slot_bytes = 4 * ((V // 2) * (n * n + n) + n * n)
+    slots = (64 << 20) // slot_bytes
+    assert slots == 16 and 20 % slots != 0
+    p = make_problem(n, 0.2, V, 1e6, B=20, seed=5)
     g = Geom.make(p.n, p.dx, p.V)
     mu_all = torch.tensor(p.mu, dtype=torch.float32, device=cuda)
     S = torch.tensor(p.S, dtype=torch.float32, device=cuda)
@@ -55,12 +64,21 @@ def test_noalloc_matches_workspace_entry_point(cuda):
         # arithmetic summed in another order
         assert rel_l2(F.cpu().numpy(), F_ref.cpu().numpy()) < 1e-5, call
         np.testing.assert_allclose(L.cpu().numpy(), L_ref.cpu().numpy(), rtol=1e-6)
+        # and against the FP64 oracle on two sampled candidates (images 1e-4,
+        # scores 1e-6 relative, as for boac_mlem)
+        for b in (0, 13):
+            Fo, Lo, _ = oracle.mlem_batch(p.geom, p.mu[order[b]][None], p.S, K)
+            assert rel_l2(F[b].cpu().numpy(), Fo[0]) < 1e-4, (call, b)
+            assert abs(L[b].item() - Lo[0]) < 1e-6 * abs(Lo[0]), (call, b)
     # arguments are still checked on the host
     F = torch.ones(20, p.n, p.n, device=cuda)
     L = torch.empty(20, dtype=torch.float64, device=cuda)
     bad = Geom.make(p.n, p.dx, 119)
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     assert lib.boac_mlem_noalloc(ctypes.byref(bad), _p(mu_all), _p(S), 0, _p(F), 2, 20, _p(L), 1,
+                                 stream) == _lib.BOAC_EINVAL
+    # L is required: a timed-out hand-over shows only as a NaN score here
+    assert lib.boac_mlem_noalloc(ctypes.byref(g), _p(mu_all), _p(S), 0, _p(F), 2, 20, None, 1,
                                  stream) == _lib.BOAC_EINVAL
 
 
