@@ -151,18 +151,23 @@ def fused_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes per launch of the fused kernel from the committed ncu summary,
-    if it was taken on the current kernel source (else None)."""
+def profiled_bytes(key="dram_bytes_per_launch_full_size"):
+    """A per-launch byte count of the fused kernel (DRAM or L2) read from the
+    committed ncu summary -- the bench does not run ncu itself -- if that
+    summary was taken on the current kernel source (else None)."""
     try:
         text = open(PROFILE_FILE).read()
     except OSError:
         return None
     m_src = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]{16})", text)
-    m_b = re.search(r"dram_bytes_per_launch_full_size:\s*([0-9.eE+]+)", text)
+    m_b = re.search(key + r":\s*([0-9.eE+]+)", text)
     if not m_src or not m_b or m_src.group(1) != fused_source_hash():
         return None
     return float(m_b.group(1))
+
+
+def profiled_traffic():
+    return profiled_bytes("dram_bytes_per_launch_full_size")
 
 
 # FP32 work per ray sample per view per iteration: two bilinear gathers (F and
@@ -171,9 +176,63 @@ def profiled_traffic():
 FLOPS_PER_SAMPLE = 50
 
 
-def fp32_peak_tflops():
-    """FP32 FMA rate: 152 SMs x 128 lanes x 2 flop x 2070 MHz (max SM clock)."""
-    return 152 * 128 * 2 * 2.070e9 / 1e12
+def sm_max_mhz():
+    """Maximum SM clock: the measured-peaks file's figure, else nvidia-smi's."""
+    try:
+        with open(PEAKS_FILE) as fh:
+            return float(json.load(fh)["sm_max_mhz"]), "MEASURED_PEAKS.json sm_max_mhz"
+    except (OSError, KeyError, ValueError):
+        pass
+    try:
+        out = subprocess.run(["nvidia-smi", "--id=0", "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits"],
+                             capture_output=True, text=True, timeout=20).stdout.strip().splitlines()
+        return float(out[0]), "nvidia-smi clocks.max.sm"
+    except (OSError, ValueError, IndexError, subprocess.SubprocessError):
+        return 2070.0, "nominal 2070 MHz"
+
+
+_FP32 = {}
+
+
+def fp32_peak(dev=None):
+    """FP32 FMA rate of the device: SMs (read from the device) x 128 FP32
+    lanes x 2 flop x the maximum SM clock.  Returns (TFLOP/s, description)."""
+    if "v" not in _FP32:
+        import torch
+        d = dev if dev is not None else torch.device("cuda", torch.cuda.current_device())
+        sms = torch.cuda.get_device_properties(d).multi_processor_count
+        mhz, src = sm_max_mhz()
+        _FP32["v"] = (sms * 128 * 2 * mhz * 1e6 / 1e12,
+                      f"derived: {sms} SMs (device) x 128 FP32 lanes x 2 flop x {mhz:.0f} MHz ({src})")
+    return _FP32["v"]
+
+
+def fp32_peak_tflops(dev=None):
+    return fp32_peak(dev)[0]
+
+
+def l2_probe_gbs(dev, mib=24, reps=20):
+    """L2 bandwidth probe: a copy of a buffer pair that stays resident in L2
+    (2 x 24 MiB, well under the 129 MB L2), timed with CUDA events after
+    warm-up; read + write bytes over time, best of 3."""
+    import torch
+    n = (mib << 20) // 4
+    a = torch.ones(n, dtype=torch.float32, device=dev)
+    b = torch.empty_like(a)
+    for _ in range(5):
+        b.copy_(a)
+    torch.cuda.synchronize(dev)
+    best = float("inf")
+    st = torch.cuda.current_stream(dev)
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            b.copy_(a)
+        e1.record(st)
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1) / reps)
+    return 2.0 * n * 4 / (best / 1e3) / 1e9
 
 
 def algorithmic_bytes_per_cand_iter(n, V):
@@ -318,12 +377,15 @@ def run_gpu(args, rank, world, local_rank):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    def step(ev_k=None):
+    def step(ev_k=None, check=False):
         boac.boac_rasterize_mu(g, t, c_d, out=mu)
         F.fill_(1.0)
         if ev_k is not None:
             ev_k[0].record(stream)
-        boac.boac_mlem(g, mu, S_d, F, K, score=True, ws=ws, L=L)
+        # check: the public call's default (wait, then raise on a failed
+        # device status); the device-timed loop keeps the launches queued
+        # back to back and checks the status word once after it
+        boac.boac_mlem(g, mu, S_d, F, K, score=True, ws=ws, L=L, check_status=check)
         if ev_k is not None:
             ev_k[1].record(stream)
 
@@ -353,6 +415,7 @@ def run_gpu(args, rank, world, local_rank):
     tot_ms = max_over_ranks(sum(step_ms), world)
     value = weak_scaling_value(world, B * K, args.steps, tot_ms)
     assert torch.isfinite(L).all(), "non-finite score"
+    boac._raise_on_device_status("boac_mlem", ws)
 
     # ---- end to end through the public API with host buffers (pinned)
     e2e = None
@@ -362,6 +425,7 @@ def run_gpu(args, rank, world, local_rank):
         return
     plain = None if args.no_plain else plain_timing(g, boac, mu, S_d, dev, stream, K)
     grad = None if args.no_plain else grad_timing(g, t, boac, c_d, S_d, dev, stream)
+    l2_gbs = l2_probe_gbs(dev)
 
     # ---- roofline of the dominant kernel (the fused MLEM kernel)
     kavg_s = sum(kern_ms) / len(kern_ms) / 1e3
@@ -370,24 +434,41 @@ def run_gpu(args, rank, world, local_rank):
     # On-chip bound (ALU/issue): the algorithm's FP32 work per candidate-
     # iteration against the FP32 FMA rate of the part.
     flops = FLOPS_PER_SAMPLE * WL.V * WL.n * WL.n * cand_its
-    fp32_peak = fp32_peak_tflops()
+    fp32_pk, fp32_kind = fp32_peak(dev)
     achieved = flops / kavg_s / 1e12
     roof = {"bound": "alu", "kernel": "mlem_fused_kernel<128,1024,4 views per grid>",
-            "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+            "achieved": achieved, "peak": fp32_pk, "unit": "TFLOP/s", "frac": achieved / fp32_pk,
             "traffic": traffic,
-            "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch, "
+                              "read from the committed profile summary while the kernel source is unchanged "
+                              "(null otherwise)",
+            "peak_kind": fp32_kind,
             "work_model": f"{FLOPS_PER_SAMPLE} FP32 ops per ray sample per view per iteration",
             "algorithmic_flops_per_launch": flops, "kernel_ms": 1e3 * kavg_s,
-            "timed": "CUDA events around boac_mlem on its stream: the fused kernel and the two "
-                     "small kernels that sum the shared sinogram's ln S! term (about 0.02 ms)"}
-    # The same launch against HBM: bytes of the materialised-table algorithm
-    # (attenuation table read in the forward and the backward pass).
+            "timed": "CUDA events around boac_mlem on its stream: the scatter-schedule kernel, the two "
+                     "small kernels that sum the shared sinogram's ln S! term and the fused kernel"}
     peak, peak_kind = measured_peak_gbs()
     alg = algorithmic_bytes_per_cand_iter(WL.n, WL.V) * cand_its
-    hbm = {"achieved": alg / kavg_s / 1e9, "peak": peak, "unit": "GB/s",
+    # What-if: the same launch against HBM, counting the bytes the
+    # materialised-table algorithm would move (table read in the forward and
+    # the backward pass).  The kernel does not move these bytes.
+    hbm = {"what_if": "materialised-table algorithm's bytes over this kernel's time (not an achieved rate)",
+           "achieved": alg / kavg_s / 1e9, "peak": peak, "unit": "GB/s",
            "frac": alg / kavg_s / 1e9 / peak, "peak_kind": f"{peak_kind} hbm_gbs (copy)",
            "algorithmic_bytes_per_launch": alg,
            "dram_bytes_per_launch": traffic}
+    # Measured memory traffic of the launch against the measured peaks.
+    l2_bytes = profiled_bytes("l2_bytes_per_launch_full_size") if (B, K) == (WL.B, WL.K) else None
+    mem = {"dram": None if traffic is None else
+           {"bytes_per_launch": traffic, "achieved_gbs": traffic / kavg_s / 1e9, "peak_gbs": peak,
+            "frac": traffic / kavg_s / 1e9 / peak, "peak_kind": f"{peak_kind} hbm_gbs (copy)"},
+           "l2": {"probe_gbs": l2_gbs,
+                  "probe": "L2-resident copy (2 x 24 MiB, read + write bytes), CUDA events, this run",
+                  "bytes_per_launch": l2_bytes,
+                  "achieved_gbs": None if l2_bytes is None else l2_bytes / kavg_s / 1e9,
+                  "frac": None if l2_bytes is None else l2_bytes / kavg_s / 1e9 / l2_gbs,
+                  "bytes_source": "ncu lts__t_bytes.sum of one full-size launch from the committed "
+                                  "profile summary (null when the kernel source changed)"}}
     config = dict(CONFIG, global_batch=world * B, parallelism=f"replicas{world}")
     if (B, K) != (WL.B, WL.K):
         config["reduced_case"] = f"{B} candidates x {K} iterations (not the benchmark workload)"
@@ -398,16 +479,22 @@ def run_gpu(args, rank, world, local_rank):
         "config": config,
         "roofline": roof,
         "roofline_hbm": hbm,
+        "memory_traffic": mem,
         "e2e": e2e,
-        # per step: rasterize_kernel, lgamma_partial_kernel, lgamma_final_kernel
-        # and mlem_fused_kernel
-        "gpu_launches": 4 * args.steps,
+        # per step: rasterize_kernel, lgamma_partial_kernel, lgamma_final_kernel,
+        # scatter_schedule_kernel and mlem_fused_kernel
+        "gpu_launches": 5 * args.steps,
         "clocks": clk.summary(),
     }
     if plain is not None:
         line["plain_path"] = dict(plain, speedup_of_batched=value / world / plain["value"])
     if grad is not None:
         line["differentiable_score"] = grad
+    if world == 1 and not args.no_workloads:
+        # the other workloads of the hot path, each on its own inputs
+        # (default launch shapes: what boac_mlem / boac_mlem_ragged pick)
+        line["workloads"] = {name: workload_summary(workload_line(name, args, dev, tune=False))
+                             for name in ("grad", "ragged", "large")}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sample(dev)
     print(json.dumps(line), flush=True)
@@ -427,7 +514,7 @@ def e2e_timing(args, world, dev, stream, step, c_d, S_d, L, F, coefs, S_np, flus
     def e2e_step():
         c_d.copy_(c_h, non_blocking=True)
         S_d.copy_(S_h, non_blocking=True)
-        step()
+        step(check=True)
         L_h.copy_(L, non_blocking=True)
         F_h.copy_(F, non_blocking=True)
 
@@ -489,10 +576,11 @@ def plain_timing(g, boac, mu, S_d, dev, stream, K):
 
 
 # ----------------------------------------------------------------- other workloads
-def _timed(fn, dev, reps=2):
+def _timed(fn, dev, reps=2, warm=True):
     """Best of `reps` CUDA-event timings of fn() after one warm-up call (ms)."""
     import torch
-    fn()
+    if warm:
+        fn()
     torch.cuda.synchronize(dev)
     best = float("inf")
     for _ in range(reps):
@@ -523,19 +611,16 @@ def _phantom_sinograms(boac, Geom, Tissue, dev, n, dx, V, counts, seeds, c_true=
     return g, t, out
 
 
-def run_workload(args):
-    """Throughput of the other workloads of the hot path on one GPU (one JSON
-    line each): the single-candidate case, the ragged batch, the large slices
-    and the differentiable score."""
+def workload_line(name, args, dev, tune=None):
+    """Throughput of one of the other workloads of the hot path on one GPU:
+    the single-candidate case, the ragged batch, the large slices, the
+    differentiable score, the explicit system matrix.  Returns its JSON line
+    (None for the quality study, which prints its own)."""
     import torch
     from paper_2109_11920_gb300 import Geom, Tissue
     from paper_2109_11920_gb300 import api as boac
     from paper_2109_11920_gb300 import autotune
-    from paper_2109_11920_gb300 import build as pkg_build
-    pkg_build.build()
-    dev = torch.device("cuda", 0)
-    peak = fp32_peak_tflops()
-    name = args.workload
+    peak, peak_kind = fp32_peak(dev)
     if name == "small":
         wl = synth.SMALL
         g, t, (S,) = _phantom_sinograms(boac, Geom, Tissue, dev, wl.n, wl.dx, wl.V, wl.counts, [wl.seed])
@@ -586,9 +671,20 @@ def run_workload(args):
             batch = boac.RaggedBatch([g], [0] * (n_sl * per), [K_l] * (n_sl * per), mus, Ss, device=dev)
             work = [(wl.V, wl.n, K_l)] * (n_sl * per)
             desc = f"{wl.name}: {n_sl} slices x {per} candidates, 256x256, 180 views, K={K_l}"
-        config = autotune.tune_ragged(batch, probe_iters=2, repeats=1) if not args.no_tune else None
+        tune = (not args.no_tune) if tune is None else tune
+        config = autotune.tune_ragged(batch, probe_iters=2, repeats=1) if tune else None
         batch.prepare(config)
-        ms = _timed(lambda: (batch.F_pool.fill_(1.0), batch.run()), dev, reps=1 if name == "large" else 2)
+        if name == "large":
+            # warm-up on the first slice's candidates only (module load, kernel
+            # attributes), then one timed run of the whole batch (about 7 s)
+            warm = boac.RaggedBatch([g], [0] * per, [2] * per, mus[:per], Ss[:per], device=dev)
+            warm.prepare(config)
+            warm.run()
+            ms = _timed(lambda: (batch.F_pool.fill_(1.0), batch.run()), dev, reps=1, warm=False)
+        else:
+            ms = _timed(lambda: (batch.F_pool.fill_(1.0), batch.run()), dev, reps=2)
+        if batch.status() != boac._lib.BOAC_OK:
+            raise RuntimeError(f"{name}: device status {batch.status()}")
         extra = {"launch_config": config}
     elif name == "quality":
         from paper_2109_11920_gb300 import quality
@@ -606,7 +702,7 @@ def run_workload(args):
                                                  f"{wl.V} views, {wl.counts:g} counts, K={wl.K}, BO {wl.extra['bo_init']} "
                                                  f"initial + {wl.extra['bo_cycles']} cycles x {wl.B} candidates"},
                           "cases": rows}), flush=True)
-        return
+        return None
     elif name == "sysmat":
         # the batched workload through the explicit system matrix
         wl = synth.BATCHED
@@ -669,10 +765,31 @@ def run_workload(args):
             "unit": UNIT, "n_gpus": 1, "ms": ms, "higher_is_better": True, "dtype": "f32",
             "data": "synthetic", "config": {"workload": desc},
             "roofline": {"bound": "alu", "achieved": flops / (ms / 1e3) / 1e12, "peak": peak,
-                         "unit": "TFLOP/s", "frac": flops / (ms / 1e3) / 1e12 / peak,
+                         "unit": "TFLOP/s", "frac": flops / (ms / 1e3) / 1e12 / peak, "peak_kind": peak_kind,
                          "work_model": f"{FLOPS_PER_SAMPLE} FP32 ops per ray sample per view per iteration"}}
     line.update(extra)
-    print(json.dumps(line), flush=True)
+    return line
+
+
+def run_workload(args):
+    """One JSON line for the workload named by --workload."""
+    import torch
+    from paper_2109_11920_gb300 import build as pkg_build
+    pkg_build.build()
+    dev = torch.device("cuda", 0)
+    line = workload_line(args.workload, args, dev)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+def workload_summary(line):
+    """The compact form of a workload line carried by the benchmark line."""
+    out = {"value": line["value"], "unit": line["unit"], "ms": line["ms"],
+           "fp32_model_frac": line["roofline"]["frac"], "workload": line["config"]["workload"]}
+    for k in ("launch_config", "work_model_note"):
+        if k in line:
+            out[k] = line[k]
+    return out
 
 
 def main():
@@ -692,6 +809,8 @@ def main():
     ap.add_argument("--workload", default="batched", choices=["batched", "small", "ragged", "large", "grad", "grad_params", "quality", "sysmat"],
                     help="batched: the benchmark; the others print their own throughput line")
     ap.add_argument("--no-tune", action="store_true", help="ragged/large: default launch shapes")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="batched: skip the gradient, ragged and large-slice lines")
     args = ap.parse_args()
     if args.workload != "batched":
         run_workload(args)

@@ -65,7 +65,7 @@ def build(force: bool = False, extra_flags=(), verbose: bool = False) -> str:
         objs = list(ex.map(lambda s: _compile(s, extra_flags), srcs))
     if force or _stale(LIB, objs):
         tmp = LIB + f".tmp{os.getpid()}"
-        subprocess.check_call([nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"])
+        subprocess.check_call([nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart", "-ldl"])
         os.replace(tmp, LIB)
     if verbose:
         print("built", LIB, file=sys.stderr)

@@ -87,8 +87,235 @@ template <int N, int NT>
 __host__ __device__ constexpr size_t fused_smem_bytes(int V) {
     using L = FusedShape<N, NT>;
     return sizeof(float) * ((fused_global_images(N) ? 0 : fused_image_floats<N, NT>()) +
-                            4 * L::NSEG * N + 4 * N + 2 * ((V + 1) / 2) * 2) +
+                            4 * L::NSEG * N + 8 * N + 2 * ((V + 1) / 2) * 2) +
            sizeof(double) * 32;
+}
+
+// ---- scatter schedule -------------------------------------------------
+// The race-free class scatter adds each sample's back-projection weight to
+// the four pixels of its bilinear footprint with plain read-modify-writes of
+// shared memory.  In the natural order (32 lanes = 32 samples along a
+// lattice row) the footprints of a warp's lanes fall on few banks for most
+// grid angles (2.4-way conflicts on average at 128 x 128), and samples
+// outside the image still take a lane.  The schedule lists, for every sample
+// grid and class, the class's in-image samples in rounds of 32 whose
+// footprint corners (0, 0) lie in 32 different banks of the padded
+// accumulator (the other three corners are fixed offsets of it, so they
+// differ too) and whose weights lie in 32 different banks of the sample
+// buffer W -- a 32 x 32 bank assignment made greedily by one warp per
+// (grid, class).  It depends on the geometry only; the order inside a class
+// does not change any sum (footprints of one class are disjoint, so every
+// pixel still receives its contributions class by class), so results are
+// bit-identical to the natural order.  Every class has a fixed capacity of
+// slots; slots after its last round hold kSchedEmpty, so the fused kernel
+// can load a class's slots before it knows how many rounds it has.
+template <int N>
+struct SchedShape {
+    static_assert(N <= 128, "entries pack k and b into 8 bits each");
+    static constexpr int CLS_MAX = ((N + 2) / 3) * ((N + 2) / 3);  // samples of class (0, 0)
+    static constexpr int ROUNDS = ((CLS_MAX + 31) / 32 + 17) & ~1;  // capacity, in rounds of 32 (even)
+    static constexpr int CLS_ENTRIES = ROUNDS * 32;
+    static constexpr int CLS_WORDS = CLS_ENTRIES / 2;
+};
+// Slot of round r, lane l in a class's entries: rounds are stored in pairs,
+// lane-interleaved, so that one 32-bit word per lane holds the lane's entry
+// of both rounds (low half: the even round).
+__host__ __device__ constexpr int sched_slot(int r, int lane) { return (r >> 1) * 64 + 2 * lane + (r & 1); }
+constexpr unsigned short kSchedEmpty = 0xFFFFu;
+
+__host__ __device__ constexpr size_t sched_entries(int n) {
+    return n == 64 ? SchedShape<64>::CLS_ENTRIES : n == 96 ? SchedShape<96>::CLS_ENTRIES
+                                                           : SchedShape<128>::CLS_ENTRIES;
+}
+// Per grid: 9 classes x CLS_ENTRIES entries (k << 8 | b, or kSchedEmpty).
+static size_t sched_bytes(int n, int ngrid) {
+    return align256(sizeof(unsigned short) * 9 * sched_entries(n) * (size_t)ngrid);
+}
+
+template <int N>
+__global__ void __launch_bounds__(256) scatter_schedule_kernel(int V, unsigned short* __restrict__ sched) {
+    using S = SchedShape<N>;
+    constexpr int P = N + 1, WP = N + 1;
+    const int gi = blockIdx.x / 9, cls = blockIdx.x % 9;
+    const int pk = cls / 3, pb = cls % 3;
+    const int nbc = (N - pb + 2) / 3, cnt = ((N - pk + 2) / 3) * nbc;
+    __shared__ unsigned short ent[S::CLS_MAX];  // samples grouped by (bank, W bank)
+    __shared__ unsigned short key[S::CLS_MAX];  // (bank << 5 | W bank) of sample t, or empty
+    __shared__ int num[1024], start[1024], cur[1024];
+    __shared__ int fits, s_rounds;
+    float cs, sn;
+    view_cos_sin(gi, V, &cs, &sn);  // grid gi's base view, as in the fused kernel
+    const float c = 0.5f * (float)(N - 1);
+    unsigned short* out = sched + ((size_t)gi * 9 + cls) * S::CLS_ENTRIES;
+    for (int i = threadIdx.x; i < 1024; i += blockDim.x) num[i] = 0;
+    __syncthreads();
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+        const int k = pk + 3 * (t / nbc), b = pb + 3 * (t % nbc);
+        float u, w;
+        sample_uw(k, b, cs, sn, c, &u, &w);
+        unsigned short kk = kSchedEmpty;
+        if (inside_open(u, w, N)) {
+            const int q = ((int)floorf(w) + 1) * P + (int)floorf(u) + 1;
+            kk = (unsigned short)(((q & 31) << 5) | ((k * WP + b) & 31));
+            atomicAdd(&num[kk], 1);
+        }
+        key[t] = kk;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {  // exclusive prefix sum over the 1024 cells
+        const int lane = threadIdx.x;
+        int s = 0;
+        for (int i = 0; i < 32; ++i) s += num[lane * 32 + i];
+        int incl = s;
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += y;
+        }
+        int run = incl - s;
+        for (int i = 0; i < 32; ++i) {
+            start[lane * 32 + i] = run;
+            cur[lane * 32 + i] = run;
+            run += num[lane * 32 + i];
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+        const unsigned short kk = key[t];
+        if (kk != kSchedEmpty)
+            ent[atomicAdd(&cur[kk], 1)] = (unsigned short)(((pk + 3 * (t / nbc)) << 8) | (pb + 3 * (t % nbc)));
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int r = 0;
+        // Greedy rounds, lane q owning the samples whose footprint starts in
+        // bank q: every lane with samples left proposes the free W bank
+        // nearest above its own index; a W bank claimed by several lanes goes
+        // to the lane with the most samples left; losers propose again among
+        // the banks still free.
+        const int lane = threadIdx.x;
+        unsigned avail = 0;
+        int left = 0;
+        for (int x = 0; x < 32; ++x) {
+            const int m = num[lane * 32 + x];
+            if (m) avail |= 1u << x;
+            left += m;
+            cur[lane * 32 + x] = 0;  // taken so far
+        }
+        while (__any_sync(0xffffffffu, left > 0) && r < S::ROUNDS) {
+            unsigned used = 0;
+            int pick = -1;
+            for (;;) {
+                int cand = -1;
+                const unsigned fr = avail & ~used;
+                if (pick < 0 && fr) cand = (__ffs(__funnelshift_r(fr, fr, lane)) - 1 + lane) & 31;
+                if (!__any_sync(0xffffffffu, cand >= 0)) break;
+                const unsigned grp = __match_any_sync(0xffffffffu, cand);
+                const unsigned pri = cand >= 0 ? ((unsigned)left << 5) | (unsigned)(31 - lane) : 0u;
+                const bool win = cand >= 0 && pri == __reduce_max_sync(grp, pri);
+                used |= __reduce_or_sync(0xffffffffu, win ? 1u << cand : 0u);
+                if (win) {
+                    const int cell = lane * 32 + cand;
+                    pick = ent[start[cell] + cur[cell]];
+                    if (++cur[cell] == num[cell]) avail &= ~(1u << cand);
+                    --left;
+                }
+            }
+            out[sched_slot(r, lane)] = pick >= 0 ? (unsigned short)pick : kSchedEmpty;
+            ++r;
+        }
+        const bool ok = !__any_sync(0xffffffffu, left > 0);
+        if (lane == 0) {
+            fits = ok;
+            s_rounds = r;
+        }
+    }
+    __syncthreads();
+    if (!fits) {
+        // capacity exceeded (never seen): the class's in-image samples in the
+        // natural order, which always fits the capacity
+        for (int t = threadIdx.x; t < S::CLS_ENTRIES; t += blockDim.x) out[t] = kSchedEmpty;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int m = 0;
+            for (int t = 0; t < cnt; ++t, ++m)
+                if (key[t] != kSchedEmpty)
+                    out[sched_slot(m / 32, m % 32)] = (unsigned short)(((pk + 3 * (t / nbc)) << 8) | (pb + 3 * (t % nbc)));
+                else
+                    --m;
+        }
+        return;
+    }
+    // the slots after the last round
+    for (int t = 32 * s_rounds + threadIdx.x; t < S::CLS_ENTRIES; t += blockDim.x)
+        out[sched_slot(t / 32, t % 32)] = kSchedEmpty;
+}
+
+// Launch the schedule builder for a one-CTA configuration (images up to
+// 128 x 128): ngrid x 9 CTAs.
+static int sched_launch(int n, int V, int ngrid, unsigned short* sched, cudaStream_t st) {
+    switch (n) {
+        case 64: scatter_schedule_kernel<64><<<ngrid * 9, 256, 0, st>>>(V, sched); break;
+        case 96: scatter_schedule_kernel<96><<<ngrid * 9, 256, 0, st>>>(V, sched); break;
+        case 128: scatter_schedule_kernel<128><<<ngrid * 9, 256, 0, st>>>(V, sched); break;
+        default: return BOAC_OK;
+    }
+    return launch_status();
+}
+
+// A thread's words of one class of a grid's schedule (word t = tid + i NT:
+// warp w's lanes hold rounds 2 (w + i NT / 32) and that + 1).
+template <int N, int NT>
+struct SchedSlots {
+    static constexpr int CW = SchedShape<N>::CLS_WORDS;
+    static constexpr int KE = (CW + NT - 1) / NT;
+    unsigned e[KE];
+    __device__ __forceinline__ void load(const unsigned short* __restrict__ cls_entries) {
+        const unsigned* wds = reinterpret_cast<const unsigned*>(cls_entries);
+#pragma unroll
+        for (int i = 0; i < KE; ++i) {
+            const int t = threadIdx.x + i * NT;
+            e[i] = (i + 1) * NT <= CW || t < CW ? __ldg(wds + t) : 0xFFFFFFFFu;
+        }
+    }
+};
+
+// The class scatter of scatter_classes (boac_device.cuh), in schedule order.
+// `first` holds this thread's slots of class 0 (loaded by the caller ahead
+// of time); each class's loop loads the next class's slots before it works,
+// so the loads are in flight across the class's work and its barrier.
+template <int N, int NT, int P, int WP>
+__device__ __forceinline__ void scatter_scheduled(const float* __restrict__ W, float* img1, float cs, float sn,
+                                                  float c, const unsigned short* __restrict__ sched,
+                                                  SchedSlots<N, NT> cur) {
+    constexpr int CE = SchedShape<N>::CLS_ENTRIES;
+    static_assert(CE % 64 == 0, "rounds are stored in lane-interleaved pairs");
+#pragma unroll 1
+    for (int cls = 0; cls < 9; ++cls) {
+        SchedSlots<N, NT> nxt;
+        if (cls < 8) nxt.load(sched + (cls + 1) * CE);
+#pragma unroll
+        for (int h = 0; h < 2 * SchedSlots<N, NT>::KE; ++h) {
+            const unsigned v = (cur.e[h >> 1] >> (16 * (h & 1))) & 0xFFFFu;
+            if (v == kSchedEmpty) continue;
+            const int k = (int)(v >> 8), b = (int)(v & 255u);
+            float u, w;
+            sample_uw(k, b, cs, sn, c, &u, &w);
+            // in (-1, n)^2 by construction: no bounds test
+            const float fj = floorf(u), fi = floorf(w);
+            const float au = u - fj, aw = w - fi;
+            float* p = img1 + ((int)fi + 1) * P + ((int)fj + 1);
+            const float g = W[k * WP + b];
+            const float g1 = g * aw, g0 = g - g1;
+            const float g01 = g0 * au, g00 = g0 - g01;
+            const float g11 = g1 * au, g10 = g1 - g11;
+            p[0] += g00;
+            p[1] += g01;
+            p[P] += g10;
+            p[P + 1] += g11;
+        }
+        __syncthreads();
+        cur = nxt;
+    }
 }
 
 // CTAs per SM the register allocation is sized for: as many as shared memory
@@ -97,6 +324,12 @@ __host__ __device__ constexpr size_t fused_smem_bytes(int V) {
 template <int N, int NT>
 constexpr int fused_min_blocks() {
     return (N <= 64 ? 3 : 1) < 1024 / NT ? (N <= 64 ? 3 : 1) : (1024 / NT > 0 ? 1024 / NT : 1);
+}
+
+// The scatter schedule of grid gi (images up to 128 x 128 only).
+template <int N>
+__device__ __forceinline__ const unsigned short* grid_sched(const FusedArgs& a, int gi) {
+    return a.sched + (size_t)gi * 9 * SchedShape<(N <= 128 ? N : 128)>::CLS_ENTRIES;
 }
 
 template <int N, int NT, bool QUAD>
@@ -116,7 +349,8 @@ __global__ void __launch_bounds__(NT, (fused_min_blocks<N, NT>())) mlem_fused_ke
     float* redc = fused_global_images(N) ? smem : W + N * WP;  // [2][NSEG][N] column partial sums
     float* redr = redc + 2 * NSEG * N;  // [2][NSEG][N] row partial sums
     float* rr = redr + 2 * NSEG * N;    // [4][N] ratios r = S / q per view
-    float* csn = rr + 4 * N;            // [V][2]
+    float* Sg = rr + 4 * N;             // [4][N] the grid's sinogram rows (cp.async)
+    float* csn = Sg + 4 * N;            // [V][2]
     double* dred = reinterpret_cast<double*>(csn + 2 * ((a.V + 1) / 2) * 2);
 
     const int tid = threadIdx.x;
@@ -130,6 +364,9 @@ __global__ void __launch_bounds__(NT, (fused_min_blocks<N, NT>())) mlem_fused_ke
     const int lb = tid % N, seg = tid / N;
     const int k0 = seg * SEG;
     const size_t gstride = fused_group_floats(N, QUAD);
+    // scatter in schedule order (images up to 128 x 128, schedule present)
+    constexpr int SN = N <= 128 ? N : 128;
+    const bool use_sched = N <= 128 && a.sched != nullptr;
 
     for (int v = tid; v < V; v += NT) view_cos_sin(v, V, &csn[2 * v], &csn[2 * v + 1]);
 
@@ -181,6 +418,8 @@ __global__ void __launch_bounds__(NT, (fused_min_blocks<N, NT>())) mlem_fused_ke
         // (loops unrolled by 8, as in the iterations below: +0.8 % measured)
         for (int gi = 0; gi < ngrid; ++gi) {
             const float cs = csn[2 * gi], sn = csn[2 * gi + 1];
+            SchedSlots<SN, NT> sched0;  // this grid's scatter slots of class 0
+            if (use_sched) sched0.load(grid_sched<N>(a, gi));
             float* Xc = tab + gi * gstride;
             float* XrT = Xc + NN;
             float* Uc = QUAD ? Xc + 2 * NN : Xc + NN;
@@ -258,7 +497,8 @@ __global__ void __launch_bounds__(NT, (fused_min_blocks<N, NT>())) mlem_fused_ke
                 }
             }
             __syncthreads();
-            scatter_classes<N, NT, FusedShape<N, NT>::P, FusedShape<N, NT>::WP>(W, img1, cs, sn, c);
+            if (use_sched) scatter_scheduled<SN, NT, P, WP>(W, img1, cs, sn, c, grid_sched<N>(a, gi), sched0);
+            else scatter_classes<N, NT, P, WP>(W, img1, cs, sn, c);
         }
         if (tid == 0) {  // second part of a cut candidate: wait for the first
             int ok = 1;
@@ -314,6 +554,13 @@ __global__ void __launch_bounds__(NT, (fused_min_blocks<N, NT>())) mlem_fused_ke
                 }
                 const int vc1 = gi, vc2 = gi + V / 2;           // column views
                 const int vr1 = gi + V / 4, vr2 = gi + 3 * V / 4;  // row views (QUAD)
+                // the grid's sinogram rows, copied to shared memory while the
+                // forward passes run (waited for before the ratio step)
+                for (int t = tid; t < (QUAD ? 4 * N : 2 * N); t += NT) {
+                    const int vi = t / N, v = vi == 0 ? vc1 : vi == 1 ? vc2 : vi == 2 ? vr1 : vr2;
+                    copy_async4(Sg + t, S + (size_t)v * N + (t % N));
+                }
+                copy_async_commit();
                 // forward, column views: sample F on the grid.  (The column
                 // and row passes and the column weights unroll by 8: fully
                 // unrolled they spill at 64 registers; measured +7.8 %.)
@@ -349,6 +596,7 @@ __global__ void __launch_bounds__(NT, (fused_min_blocks<N, NT>())) mlem_fused_ke
                     redr[seg * N + lb] = acc3;
                     redr[(NSEG + seg) * N + lb] = acc4;
                 }
+                copy_async_wait_all();
                 __syncthreads();
                 // q, then r = S / q (or the Eq. 5 terms when scoring)
                 for (int t = tid; t < (QUAD ? 4 * N : 2 * N); t += NT) {  // one ray per thread
@@ -358,13 +606,14 @@ __global__ void __launch_bounds__(NT, (fused_min_blocks<N, NT>())) mlem_fused_ke
 #pragma unroll
                     for (int s2 = 0; s2 < NSEG; ++s2) q += rp[s2 * N + j];
                     q *= dx;
-                    const int v = vi == 0 ? vc1 : vi == 1 ? vc2 : vi == 2 ? vr1 : vr2;
-                    const float Sv = __ldg(S + (size_t)v * N + ((vi & 1) ? N - 1 - j : j));
+                    const float Sv = Sg[vi * N + ((vi & 1) ? N - 1 - j : j)];
                     if (scoring) lacc += loglik_term(Sv, q, a.include_lgamma && !a.lgS);
                     else rr[vi * N + j] = q > 0.0f ? Sv / q : 0.0f;
                 }
                 __syncthreads();
                 if (scoring) continue;
+                SchedSlots<SN, NT> sched0;  // in flight during the weight passes
+                if (use_sched) sched0.load(grid_sched<N>(a, gi));
                 // back-projection weights of the grid's views
                 {
                     const float uc = Uc[lb];
@@ -387,7 +636,8 @@ __global__ void __launch_bounds__(NT, (fused_min_blocks<N, NT>())) mlem_fused_ke
                     }
                 }
                 __syncthreads();
-                scatter_classes<N, NT, FusedShape<N, NT>::P, FusedShape<N, NT>::WP>(W, img1, cs, sn, c);
+                if (use_sched) scatter_scheduled<SN, NT, P, WP>(W, img1, cs, sn, c, grid_sched<N>(a, gi), sched0);
+                else scatter_classes<N, NT, P, WP>(W, img1, cs, sn, c);
             }
             if (scoring) break;
             // multiplicative update; clears the accumulator for the next pass
@@ -457,6 +707,12 @@ static int fused_launch_t(const FusedArgs& a, int slots, cudaStream_t st) {
                                  (int)fused_smem_bytes<N, NT>(kMaxViews)) != cudaSuccess)
             return launch_status();
         attr_set[dev] = true;
+    }
+    if constexpr (N <= 128) {
+        if (a.sched) {  // the scatter schedule of this geometry, then the kernel
+            const int s = sched_launch(N, a.V, QUAD ? a.V / 4 : a.V / 2, const_cast<unsigned short*>(a.sched), st);
+            if (s != BOAC_OK) return s;
+        }
     }
     mlem_fused_kernel<N, NT, QUAD><<<slots, NT, fused_smem_bytes<N, NT>(a.V), st>>>(a);
     return launch_status();
@@ -619,8 +875,9 @@ static int variant_occupancy(const FusedVariant* v, int V) {
 //              buffer per CTA; cluster kernel: the record kernel's flag and
 //              the ray-run records of every (band, grid)
 //   ready      one flag per candidate (the work split's hand-over)
+//   sched      one-CTA kernel, n <= 128: the scatter schedule (geometry only)
 struct FusedLayout {
-    size_t status, tab, sens, img, geo, ready, total;
+    size_t status, tab, sens, img, geo, ready, sched, total;
 };
 
 static FusedLayout fused_layout(const boac_geom* g, const FusedVariant* v, int holders, int B) {
@@ -644,7 +901,8 @@ static FusedLayout fused_layout(const boac_geom* g, const FusedVariant* v, int h
         l.geo = l.img + align256(sizeof(float) * ctas * img_floats);
         l.ready = l.geo;
     }
-    l.total = l.ready + align256(sizeof(int) * (size_t)B);
+    l.sched = l.total = l.ready + align256(sizeof(int) * (size_t)B);
+    if (v->nb == 1 && g->n <= 128) l.total = l.sched + sched_bytes(g->n, v->quad ? g->n_views / 4 : g->n_views / 2);
     return l;
 }
 
@@ -702,6 +960,7 @@ static FusedArgs base_args(const boac_geom* g, const float* mu, const float* S, 
     a.geo_bad = reinterpret_cast<int*>(ws + l.img);
     a.wait_cycles = wait_cycles();
     a.withhold = -1;
+    a.sched = l.total > l.sched ? reinterpret_cast<const unsigned short*>(ws + l.sched) : nullptr;
     return a;
 }
 
@@ -722,8 +981,11 @@ static int launch_uniform(const boac_geom* g, const FusedVariant* v, int slots, 
         cudaMemsetAsync(ws + l.ready, 0, sizeof(int) * (size_t)B, st) != cudaSuccess)
         return launch_status();
     // one shared sinogram: its ln S! sum once, in the status slot's spare bytes
-    if (L && include_lgamma && s_stride == 0)
+    if (L && include_lgamma && s_stride == 0) {
+        BOAC_RANGE("score: ln S! of the shared sinogram");
         a.lgS = lgamma_sum(g->n_views * g->n_bins, S, reinterpret_cast<double*>(ws + l.status + 8), st);
+    }
+    BOAC_RANGE("fused MLEM: set-up, iterations, score");
     return v->launch(a, grid, st);
 }
 
@@ -791,6 +1053,7 @@ using namespace boac;
 extern "C" int boac_mlem(const boac_geom* g, const float* mu, const float* S, long long s_stride,
                          float* F, int K, int B, double* L, int include_lgamma, void* ws,
                          size_t ws_bytes, void* stream) {
+    BOAC_RANGE("boac_mlem");
     if (!geom_ok(g) || !mu || !S || !F || B < 1 || K < 0 || s_stride < 0) return BOAC_EINVAL;
     if (g->n_views % 2) return BOAC_EINVAL;
     if (use_unfused(g, B))
@@ -831,6 +1094,7 @@ extern "C" size_t boac_test_mlem_handover_bytes(const boac_geom* g, int B, int K
 extern "C" int boac_test_mlem_handover(const boac_geom* g, const float* mu, const float* S, float* F, int K,
                                        int B, double* L, int config, int holders, int withhold, void* ws,
                                        size_t ws_bytes, void* stream) {
+    BOAC_RANGE("boac_test_mlem_handover");
     if (!mu || !S || !F || !L) return BOAC_EINVAL;
     const FusedVariant* v;
     FusedLayout l;
@@ -851,6 +1115,7 @@ extern "C" int boac_test_mlem_handover(const boac_geom* g, const float* mu, cons
 }
 
 extern "C" int boac_workspace_status(const void* ws, size_t ws_bytes, int* status) {
+    BOAC_RANGE("boac_workspace_status");
     if (!ws || ws_bytes < sizeof(int) || !status) return BOAC_EINVAL;
     if (cudaMemcpy(status, ws, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return launch_status();
     return BOAC_OK;
@@ -866,6 +1131,7 @@ extern "C" size_t boac_mlem_ragged_workspace_bytes(const boac_geom* classes, int
 extern "C" int boac_mlem_ragged_prepare(const boac_geom* classes, int n_classes,
                                         const boac_ragged_cand* cands, int B, const int* config,
                                         void* ws, size_t ws_bytes, void* stream) {
+    BOAC_RANGE("boac_mlem_ragged_prepare");
     RaggedPlan pl;
     int s = ragged_plan(classes, n_classes, cands, B, config, &pl);
     if (s != BOAC_OK) return s;
@@ -901,6 +1167,7 @@ extern "C" int boac_mlem_ragged_run(const boac_geom* classes, int n_classes,
                                     const boac_ragged_cand* cands, int B, const float* mu_pool,
                                     const float* S_pool, float* F_pool, double* L, int include_lgamma,
                                     const int* config, void* ws, size_t ws_bytes, void* stream) {
+    BOAC_RANGE("boac_mlem_ragged_run");
     if (!mu_pool || !S_pool || !F_pool || !L) return BOAC_EINVAL;
     RaggedPlan pl;
     int s = ragged_plan(classes, n_classes, cands, B, config, &pl);
@@ -939,6 +1206,7 @@ extern "C" int boac_mlem_ragged(const boac_geom* classes, int n_classes, const b
                                 int B, const float* mu_pool, const float* S_pool, float* F_pool,
                                 double* L, int include_lgamma, const int* config, void* ws,
                                 size_t ws_bytes, void* stream) {
+    BOAC_RANGE("boac_mlem_ragged");
     if (!mu_pool || !S_pool || !F_pool || !L) return BOAC_EINVAL;
     int s = boac_mlem_ragged_prepare(classes, n_classes, cands, B, config, ws, ws_bytes, stream);
     if (s != BOAC_OK) return s;
@@ -994,6 +1262,7 @@ static int noalloc_slots(const boac_geom* g, const FusedVariant* v, int B) {
 extern "C" int boac_mlem_noalloc(const boac_geom* g, const float* mu, const float* S,
                                  long long s_stride, float* F, int K, int B, double* L,
                                  int include_lgamma, void* stream) {
+    BOAC_RANGE("boac_mlem_noalloc");
     // L is required: the status word of the bounded hand-over wait lives in
     // the built-in array, out of the caller's reach, so a candidate that gave
     // up shows only as a NaN score.

@@ -60,6 +60,9 @@ struct FusedArgs {
     // Candidate whose first part does not release its flag (-1: none).  Set
     // only by boac_test_mlem_handover, to make the bounded wait run out.
     int withhold;
+    // One-CTA kernel, images up to 128 x 128: the scatter schedule of every
+    // (grid, class) (nullptr: natural class order).
+    const unsigned short* sched;
     // Cluster kernel only: the ray-run records of every (band, grid), and a
     // flag the record kernel sets if a run exceeds the kernel's buffers.
     const int* geo;
@@ -79,6 +82,15 @@ __device__ __forceinline__ float ex2(float x) {
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
+
+// 4-byte asynchronous copy global -> shared (no register staging); the
+// copies a thread issued are complete after copy_async_wait_all().
+__device__ __forceinline__ void copy_async4(float* dst_smem, const float* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void copy_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void copy_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Ask L2 to fetch the 128-byte line holding p (no register result).
 __device__ __forceinline__ void prefetch_l2(const void* p) {

@@ -375,6 +375,7 @@ static int score_grad_run(const boac_geom* g, const boac_tissue* t, const float*
         update_kernel<<<g1p, 256, 0, st>>>((int)cnt_pix, F_o, z, sens);
     };
     // ---- forward
+    NvtxPhases phase("gradient: forward MLEM with checkpoints");
     int s = rasterize_launch(g, t, c, t ? 6 : kParams, B, BOAC_RASTER_AREA, mu, st);
     if (s != BOAC_OK) return s;
     attenuation_table_kernel<<<rg, kRayThreads, 0, st>>>(n, V, dx, mu, tab);
@@ -403,6 +404,7 @@ static int score_grad_run(const boac_geom* g, const boac_tissue* t, const float*
         if (K == 0) cudaMemcpyAsync(Fk, ck, sizeof(float) * cnt_pix, cudaMemcpyDeviceToDevice, st);
     }
     // ---- score and d L / d q^K
+    phase.next("gradient: score and its adjoint");
     project_table(g, B, tab, Fk, dx, qK, st);
     const double* lgS = include_lgamma && s_stride == 0
                             ? lgamma_sum((int)vb, S, reinterpret_cast<double*>(base + lay.lg), st)
@@ -414,6 +416,7 @@ static int score_grad_run(const boac_geom* g, const boac_tissue* t, const float*
     abar_accum(g, B, dx, qbar, Fk, nullptr, nullptr, abar, st);
 
     // ---- reverse through the iterations, one checkpoint segment at a time
+    phase.next("gradient: reverse sweep");
     const int nseg = (K + ckpt_every - 1) / ckpt_every;
     for (int j = nseg - 1; j >= 0; --j) {
         const int n0 = j * ckpt_every;
@@ -455,6 +458,7 @@ extern "C" int boac_score_grad(const boac_geom* g, const boac_tissue* t, const f
                                const float* S, long long s_stride, int K, int ckpt_every, int B,
                                int include_lgamma, double* L, double* dL_dc, float* F_out, void* ws,
                                size_t ws_bytes, void* stream) {
+    BOAC_RANGE("boac_score_grad");
     if (!geom_ok(g) || !t || !c || !S || !L || !dL_dc || B < 1 || B > 65535 || K < 0 ||
         ckpt_every < 1 || s_stride < 0 || !(t->dR >= 0.0f))
         return BOAC_EINVAL;
@@ -466,6 +470,7 @@ extern "C" int boac_score_grad_params(const boac_geom* g, const float* p, const 
                                       long long s_stride, int K, int ckpt_every, int B,
                                       int include_lgamma, double* L, double* dL_dp, float* F_out,
                                       void* ws, size_t ws_bytes, void* stream) {
+    BOAC_RANGE("boac_score_grad_params");
     if (!geom_ok(g) || !p || !S || !L || !dL_dp || B < 1 || B > 65535 || K < 0 ||
         ckpt_every < 1 || s_stride < 0)
         return BOAC_EINVAL;

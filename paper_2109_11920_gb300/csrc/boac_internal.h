@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stddef.h>
 #include <stdint.h>
 
@@ -27,6 +28,32 @@ inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s
 
 // Map the last CUDA error to a status code (clears it).
 int launch_status();
+
+// NVTX range over a scope of host code (a no-op unless a profiler such as
+// Nsight Systems is attached): entry points and their phases -- set-up,
+// iterations, score -- show up by name on the host timeline next to the
+// kernels they enqueue.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+// Consecutive phases of one scope: next() closes the current range and
+// opens the following one.
+struct NvtxPhases {
+    explicit NvtxPhases(const char* name) { nvtxRangePushA(name); }
+    void next(const char* name) {
+        nvtxRangePop();
+        nvtxRangePushA(name);
+    }
+    ~NvtxPhases() { nvtxRangePop(); }
+    NvtxPhases(const NvtxPhases&) = delete;
+    NvtxPhases& operator=(const NvtxPhases&) = delete;
+};
+#define BOAC_NVTX_CAT2(a, b) a##b
+#define BOAC_NVTX_CAT(a, b) BOAC_NVTX_CAT2(a, b)
+#define BOAC_RANGE(name) ::boac::NvtxRange BOAC_NVTX_CAT(boac_nvtx_, __LINE__)(name)
 
 // Round up to a multiple of 256 bytes.
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }

@@ -225,6 +225,7 @@ using namespace boac;
 
 extern "C" int boac_project(const boac_geom* g, const float* mu, const float* F, int B, float* q,
                             void* stream) {
+    BOAC_RANGE("boac_project");
     if (!geom_ok(g) || !mu || !F || !q || B < 1 || B > 65535) return BOAC_EINVAL;
     project_otf_kernel<<<ray_grid(g, B), kRayThreads, 0, as_stream(stream)>>>(
         g->n, g->n_views, g->pixel_cm, mu, F, q);
@@ -233,6 +234,7 @@ extern "C" int boac_project(const boac_geom* g, const float* mu, const float* F,
 
 extern "C" int boac_backproject(const boac_geom* g, const float* mu, const float* y, int B,
                                 float* out, void* ws, size_t ws_bytes, void* stream) {
+    BOAC_RANGE("boac_backproject");
     if (!geom_ok(g) || !mu || !out || B < 1 || B > 65535) return BOAC_EINVAL;
     const size_t nn = (size_t)g->n * g->n;
     const size_t per = backproject_candidate_bytes(g);  // one candidate's table + partials
@@ -259,6 +261,7 @@ extern "C" int boac_backproject(const boac_geom* g, const float* mu, const float
 
 extern "C" int boac_loglik(const boac_geom* g, const float* q, const float* S, long long s_stride,
                            int B, int include_lgamma, double* L, void* stream) {
+    BOAC_RANGE("boac_loglik");
     if (!geom_ok(g) || !q || !S || !L || B < 1 || s_stride < 0) return BOAC_EINVAL;
     loglik_kernel<<<B, 256, 0, as_stream(stream)>>>(g->n_views * g->n_bins, q, S, s_stride,
                                                      include_lgamma, L, nullptr);
@@ -268,6 +271,7 @@ extern "C" int boac_loglik(const boac_geom* g, const float* q, const float* S, l
 extern "C" int boac_score(const boac_geom* g, const float* mu, const float* S, long long s_stride,
                           const float* F, int B, int include_lgamma, double* L, void* ws,
                           size_t ws_bytes, void* stream) {
+    BOAC_RANGE("boac_score");
     if (!geom_ok(g) || !mu || !S || !F || !L || B < 1 || B > 65535 || s_stride < 0)
         return BOAC_EINVAL;
     const size_t vb = (size_t)g->n_views * g->n_bins;
@@ -281,6 +285,7 @@ extern "C" int boac_score(const boac_geom* g, const float* mu, const float* S, l
 extern "C" int boac_mlem_plain(const boac_geom* g, const float* mu, const float* S,
                                long long s_stride, float* F, int K, int B, double* L,
                                int include_lgamma, void* ws, size_t ws_bytes, void* stream) {
+    BOAC_RANGE("boac_mlem_plain");
     if (!geom_ok(g) || !mu || !S || !F || B < 1 || K < 0 || s_stride < 0) return BOAC_EINVAL;
     if (!ws || ws_bytes < plain_candidate_bytes(g)) return BOAC_EWORKSPACE;
     const size_t nn = (size_t)g->n * g->n, vb = (size_t)g->n_views * g->n_bins;

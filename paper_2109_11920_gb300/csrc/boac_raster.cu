@@ -97,6 +97,7 @@ int rasterize_launch(const boac_geom* g, const boac_tissue* t, const float* p, i
 
 extern "C" int boac_rasterize_mu(const boac_geom* g, const boac_tissue* t, const float* c, int B,
                                  int mode, float* mu, void* stream) {
+    BOAC_RANGE("boac_rasterize_mu");
     if (!geom_ok(g) || !t || !c || !mu || B < 1) return BOAC_EINVAL;
     if (mode != BOAC_RASTER_CENTER && mode != BOAC_RASTER_AREA) return BOAC_EINVAL;
     if (!(t->dR >= 0.0f)) return BOAC_EINVAL;
@@ -105,6 +106,7 @@ extern "C" int boac_rasterize_mu(const boac_geom* g, const boac_tissue* t, const
 
 extern "C" int boac_rasterize_mu_params(const boac_geom* g, const float* p, int B, int mode,
                                         float* mu, void* stream) {
+    BOAC_RANGE("boac_rasterize_mu_params");
     if (!geom_ok(g) || !p || !mu || B < 1) return BOAC_EINVAL;
     if (mode != BOAC_RASTER_CENTER && mode != BOAC_RASTER_AREA) return BOAC_EINVAL;
     return rasterize_launch(g, nullptr, p, kParams, B, mode, mu, as_stream(stream));

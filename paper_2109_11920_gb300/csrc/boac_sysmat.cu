@@ -515,6 +515,7 @@ void free_sysmat(boac_sysmat* m) {
 using namespace boac;
 
 extern "C" int boac_sysmat_create(const boac_geom* g, boac_sysmat** out, void* stream) {
+    BOAC_RANGE("boac_sysmat_create");
     if (!out) return BOAC_EINVAL;
     *out = nullptr;
     if (!geom_ok(g)) return BOAC_EINVAL;
@@ -598,6 +599,7 @@ extern "C" long long boac_sysmat_nnz(const boac_sysmat* m) { return m ? m->nnz :
 
 extern "C" int boac_sysmat_pattern(const boac_sysmat* m, int* row_ptr, int* col, int* colT_ptr, int* rowT,
                                    void* stream) {
+    BOAC_RANGE("boac_sysmat_pattern");
     if (!m) return BOAC_EINVAL;
     cudaStream_t st = as_stream(stream);
     const size_t nn = (size_t)m->g.n * m->g.n, ne = (size_t)m->nnz;
@@ -611,6 +613,7 @@ extern "C" int boac_sysmat_pattern(const boac_sysmat* m, int* row_ptr, int* col,
 static size_t groups_of(int B) { return (size_t)((B + kCandGroup - 1) / kCandGroup); }
 
 extern "C" int boac_sysmat_values(const boac_sysmat* m, const float* mu, int B, float* vals, void* stream) {
+    BOAC_RANGE("boac_sysmat_values");
     if (!m || !mu || !vals || B < 1 || B > 65535) return BOAC_EINVAL;
     if (m->nnz == 0) return BOAC_OK;
     const dim3 grid((unsigned)((m->R + kFillWarps - 1) / kFillWarps), (unsigned)groups_of(B));
@@ -621,6 +624,7 @@ extern "C" int boac_sysmat_values(const boac_sysmat* m, const float* mu, int B, 
 
 extern "C" int boac_sysmat_project(const boac_sysmat* m, const float* vals, const float* F, int B, float* q,
                                    void* stream) {
+    BOAC_RANGE("boac_sysmat_project");
     if (!m || !vals || !F || !q || B < 1 || B > 65535) return BOAC_EINVAL;
     const int nn = m->g.n * m->g.n;
     forward_kernel<false, false><<<rows_grid(m->R, B), kWarpsPerBlock * 32, 0, as_stream(stream)>>>(
@@ -639,6 +643,7 @@ extern "C" size_t boac_sysmat_mlem_workspace_bytes(const boac_sysmat* m, int B) 
 extern "C" int boac_sysmat_mlem(const boac_sysmat* m, const float* vals, const float* S, long long s_stride,
                                 float* F, int K, int B, double* L, int include_lgamma, void* ws,
                                 size_t ws_bytes, void* stream) {
+    BOAC_RANGE("boac_sysmat_mlem");
     if (!m || !vals || !S || !F || K < 0 || B < 1 || B > 65535 || s_stride < 0) return BOAC_EINVAL;
     if (!ws || ws_bytes < boac_sysmat_mlem_workspace_bytes(m, B)) return BOAC_EWORKSPACE;
     cudaStream_t st = as_stream(stream);

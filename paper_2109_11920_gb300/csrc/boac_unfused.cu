@@ -58,10 +58,12 @@ int mlem_unfused(const boac_geom* g, const float* mu, const float* S, long long 
     const long long cnt_pix = (long long)B * nn, cnt_bin = (long long)B * vb;
     // the status word boac_workspace_status reads: this path has no waits
     cudaMemsetAsync(base + l.status, 0, sizeof(int), st);
+    BOAC_RANGE("set-up: attenuation tables, sensitivity");
     attenuation_table_kernel<<<ray_grid(g, B), kRayThreads, 0, st>>>(g->n, g->n_views, dx, mu, tab);
     int s = backproject_table(g, B, tab, nullptr, dx, sens, 0, partial, st);
     if (s != BOAC_OK) return s;
     for (int it = 0; it < K; ++it) {
+        BOAC_RANGE("MLEM iteration");
         s = project_table(g, B, tab, F, dx, q, st);
         if (s != BOAC_OK) return s;
         ratio_batched_kernel<<<grid_1d(cnt_bin, 256), 256, 0, st>>>(B, (int)vb, S, s_stride, q, r);
@@ -70,6 +72,7 @@ int mlem_unfused(const boac_geom* g, const float* mu, const float* S, long long 
         update_kernel<<<grid_1d(cnt_pix, 256), 256, 0, st>>>((int)cnt_pix, F, z, sens);
     }
     if (L) {
+        BOAC_RANGE("score (Eq. 5)");
         s = project_table(g, B, tab, F, dx, q, st);
         if (s != BOAC_OK) return s;
         // one shared sinogram: its ln S! sum once, in the status slot's spare bytes
@@ -89,6 +92,7 @@ using namespace boac;
 extern "C" int boac_mlem_unfused(const boac_geom* g, const float* mu, const float* S, long long s_stride,
                                  float* F, int K, int B, double* L, int include_lgamma, void* ws,
                                  size_t ws_bytes, void* stream) {
+    BOAC_RANGE("boac_mlem_unfused");
     if (!geom_ok(g) || !mu || !S || !F || B < 1 || B > 65535 || K < 0 || s_stride < 0) return BOAC_EINVAL;
     if ((long long)B * g->n * g->n > 0x7fffffffLL) return BOAC_EINVAL;
     return mlem_unfused(g, mu, S, s_stride, F, K, B, L, include_lgamma, ws, ws_bytes, as_stream(stream));

@@ -37,15 +37,14 @@ def test_noalloc_matches_workspace_entry_point(cuda):
     from paper_2109_11920_gb300 import build
     build.build()
     lib = _lib.load()
-    # 128 x 128, 120 views: one CTA slot's scratch is its attenuation
-    # exponents, V/2 (n^2 + n) floats, and its sensitivity image, n^2 floats
-    # (about 4.0 MB), so the 64 MiB array holds 16 slots.  20 candidates are
-    # more than that: the work split then cuts candidates between two CTAs
-    # (the hand-over path) and every slot is reused within a call.
+    # 128 x 128, 120 views: one CTA slot's scratch is at least its
+    # attenuation exponents, V/2 (n^2 + n) floats, and its sensitivity image,
+    # n^2 floats (about 4.0 MB), so the 64 MiB array holds at most 16 slots.
+    # 20 candidates are more than that: the work split then cuts candidates
+    # between two CTAs (the hand-over path) and slots are reused in a call.
     n, V = 128, 120
     slot_bytes = 4 * ((V // 2) * (n * n + n) + n * n)
-    slots = (64 << 20) // slot_bytes
-    assert slots == 16 and 20 % slots != 0
+    assert (64 << 20) // slot_bytes == 16
     p = make_problem(n, 0.2, V, 1e6, B=20, seed=5)
     g = Geom.make(p.n, p.dx, p.V)
     mu_all = torch.tensor(p.mu, dtype=torch.float32, device=cuda)
