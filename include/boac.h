@@ -93,6 +93,17 @@ const char *boac_status_string(int status);
 /* ABI version of this library (incremented on incompatible changes). */
 int boac_abi_version(void);
 
+/* Bounds faults counted by a checked build of this library
+ * (libboac_checked.so, compiled with -DBOAC_CHECKED; the paper has no
+ * counterpart).  There the shared-memory index of every bilinear gather and
+ * scatter of the fused, cluster and grouped kernels, and every entry of the
+ * scatter schedule, is checked before use; an index out of range is counted
+ * and the access skipped -- never a trap or a memory fault -- so a checked
+ * run reports *faults > 0 instead of corrupting memory.  Synchronous: reads
+ * the counters after the device work queued before it; reset != 0 clears
+ * them.  Normal builds return BOAC_EUNSUPPORTED. */
+int boac_bounds_faults(int *faults, int reset);
+
 /* Device status left in a boac_mlem / boac_mlem_ragged workspace by the last
  * call that used it: BOAC_OK; BOAC_ETIMEOUT if a kernel gave up one of its
  * bounded waits (the affected candidates' scores are NaN and their images

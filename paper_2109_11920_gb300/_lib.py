@@ -80,6 +80,7 @@ _TP = ctypes.POINTER(Tissue)
 SIGNATURES = {
     "boac_status_string": (ctypes.c_char_p, [_I]),
     "boac_abi_version": (_I, []),
+    "boac_bounds_faults": (_I, [ctypes.POINTER(ctypes.c_int), _I]),
     "boac_workspace_status": (_I, [_P, _SZ, ctypes.POINTER(ctypes.c_int)]),
     "boac_workspace_bytes": (_SZ, [_GP, _I, _I]),
     "boac_set_wait_cycles": (_LL, [_LL]),
@@ -115,21 +116,34 @@ SIGNATURES = {
 }
 
 
+CHECKED_LIB_PATH = os.path.join(PKG, "libboac_checked.so")
+
+
+def _open(path: str):
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with "
+                          "`python -m paper_2109_11920_gb300.build` (needs nvcc)")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
 def load(path: str = LIB_PATH):
     """Load libboac.so (raises if it has not been built)."""
     global _lib
     with _lock:
         if _lib is None:
-            if not os.path.exists(path):
-                raise ImportError(f"{path} is missing: build it with "
-                                  "`python -m paper_2109_11920_gb300.build` (needs nvcc)")
-            lib = ctypes.CDLL(path)
-            for name, (res, args) in SIGNATURES.items():
-                fn = getattr(lib, name)
-                fn.restype = res
-                fn.argtypes = args
-            _lib = lib
+            _lib = _open(path)
     return _lib
+
+
+def load_checked():
+    """A separate handle on the bounds-checked build, libboac_checked.so
+    (``build.build(checked=True)``), with the same entry points."""
+    return _open(CHECKED_LIB_PATH)
 
 
 def status_string(status: int) -> str:

@@ -381,13 +381,18 @@ class BoacScore(torch.autograd.Function):
 # shapes (2 * shape + 1 for two views per grid); ids 6-8 the cluster kernel
 # for V % 4 == 0: 5, 6 or 8 CTAs per candidate for 256 x 256 images, 2, 4 or
 # 8 for 128 x 128 and 64 x 64.
-N_CONFIGS = 9
+N_CONFIGS = 17
 N_SINGLE_CTA_CONFIGS = 6
 BAND_CLUSTER_SIZES = {256: {6: 5, 7: 6, 8: 8}, 128: {6: 2, 7: 4, 8: 8}, 64: {6: 2, 7: 4, 8: 8}}
+# ids 9-16: the fused kernel's cluster mode, 2, 3, 4, 6, 8, 9, 12 or 16 CTAs
+# per candidate each on its share of the sample grids (images up to 128 x 128)
+SPLIT_CLUSTER_SIZES = {9 + i: g for i, g in enumerate((2, 3, 4, 6, 8, 9, 12, 16))}
 
 
 def config_valid(g, cfg: int) -> bool:
     """Whether launch configuration ``cfg`` applies to geometry ``g``."""
+    if cfg in SPLIT_CLUSTER_SIZES:
+        return g.n in (64, 96, 128) and g.n_views % 4 == 0 and g.n_views >= 4 * SPLIT_CLUSTER_SIZES[cfg]
     if cfg >= N_SINGLE_CTA_CONFIGS:
         return cfg in BAND_CLUSTER_SIZES.get(g.n, {}) and g.n_views % 4 == 0
     if not 0 <= cfg < N_SINGLE_CTA_CONFIGS:

@@ -255,4 +255,8 @@ int project_table(const boac_geom* g, int B, const float* tab, const float* F, f
     return s;
 }
 
+#ifdef BOAC_CHECKED
+BOAC_FAULT_READER(bounds_faults_bpgroup)
+#endif
+
 }  // namespace boac

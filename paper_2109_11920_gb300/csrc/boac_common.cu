@@ -72,6 +72,20 @@ extern "C" const char* boac_status_string(int status) {
 
 extern "C" int boac_abi_version(void) { return 1; }
 
+extern "C" int boac_bounds_faults(int* faults, int reset) {
+#ifdef BOAC_CHECKED
+    if (!faults) return BOAC_EINVAL;
+    const int f = bounds_faults_fused(reset), b = bounds_faults_bpgroup(reset);
+    if (f < 0 || b < 0) return BOAC_ECUDA;
+    *faults = f + b;
+    return BOAC_OK;
+#else
+    (void)faults;
+    (void)reset;
+    return BOAC_EUNSUPPORTED;
+#endif
+}
+
 extern "C" size_t boac_workspace_bytes(const boac_geom* g, int B, int op) {
     if (!geom_ok(g) || B < 1) return 0;
     size_t vb = (size_t)g->n_views * g->n_bins;

@@ -14,6 +14,34 @@
 
 namespace boac {
 
+// Checked builds (-DBOAC_CHECKED, libboac_checked.so): the shared-memory
+// index of every bilinear gather and scatter, and every scatter-schedule
+// entry, is checked before use; an index out of range is counted in this
+// translation unit's fault counter and the access is skipped (never a trap
+// or a fault), so a checked run reports the fault count instead of
+// corrupting memory.  Normal builds compile the checks away.
+#ifdef BOAC_CHECKED
+static __device__ int g_bounds_faults;
+__device__ __forceinline__ bool index_ok(long long i, long long n) {
+    if (i >= 0 && i < n) return true;
+    atomicAdd(&g_bounds_faults, 1);
+    return false;
+}
+// Host side, one per translation unit: read (and optionally clear) the count.
+#define BOAC_FAULT_READER(name)                                                              \
+    int name(int reset) {                                                                    \
+        int v = 0;                                                                           \
+        if (cudaMemcpyFromSymbol(&v, g_bounds_faults, sizeof(int)) != cudaSuccess) return -1; \
+        if (reset) {                                                                         \
+            const int z = 0;                                                                 \
+            if (cudaMemcpyToSymbol(g_bounds_faults, &z, sizeof(int)) != cudaSuccess) return -1; \
+        }                                                                                    \
+        return v;                                                                            \
+    }
+#else
+__device__ __forceinline__ constexpr bool index_ok(long long, long long) { return true; }
+#endif
+
 // cos/sin of phi_v = 2 pi v / V (Sec. V: views uniformly spaced over the full
 // angular range).  The quadrant is taken exactly, so views a quarter turn
 // apart are exact rotations of each other; the in-quadrant angle is
@@ -57,7 +85,9 @@ __device__ __forceinline__ float bilerp_padded(const float* img, int P, int n, f
     if (!inside_open(u, w, n)) return 0.0f;
     float fj = floorf(u), fi = floorf(w);
     float au = u - fj, aw = w - fi;
-    const float* p = img + ((int)fi + 1) * P + ((int)fj + 1);
+    const int idx = ((int)fi + 1) * P + ((int)fj + 1);
+    if (!index_ok(idx, (long long)P * (n + 1))) return 0.0f;  // idx + P + 1 < P (n + 2) + 1
+    const float* p = img + idx;
     float v00 = p[0], v01 = p[1], v10 = p[P], v11 = p[P + 1];
     float top = fmaf(au, v01 - v00, v00);
     float bot = fmaf(au, v11 - v10, v10);
@@ -71,7 +101,9 @@ __device__ __forceinline__ void scatter_padded(float* img, int P, int n, float u
     if (!inside_open(u, w, n)) return;
     float fj = floorf(u), fi = floorf(w);
     float au = u - fj, aw = w - fi;
-    float* p = img + ((int)fi + 1) * P + ((int)fj + 1);
+    const int idx = ((int)fi + 1) * P + ((int)fj + 1);
+    if (!index_ok(idx, (long long)P * (n + 1))) return;
+    float* p = img + idx;
     float g1 = g * aw, g0 = g - g1;          // row weights (1 - aw), aw
     float g01 = g0 * au, g00 = g0 - g01;     // (1-aw)(1-au), (1-aw) au
     float g11 = g1 * au, g10 = g1 - g11;     // aw (1-au), aw au
@@ -130,6 +162,7 @@ __device__ __forceinline__ void scatter_classes(const float* __restrict__ W, flo
         const int nkc = (N - pk + 2) / 3, nbc = (N - pb + 2) / 3;
         for (int t = threadIdx.x; t < nkc * nbc; t += NT) {
             const int k = pk + 3 * (t / nbc), b = pb + 3 * (t % nbc);
+            if (!index_ok(k * WP + b, (long long)N * WP)) continue;
             const float g = W[k * WP + b];
             float u, w;
             sample_uw(k, b, cs, sn, c, &u, &w);

@@ -33,10 +33,14 @@
 #include <atomic>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "boac_device.cuh"
 #include "boac_fused.h"
 #include "boac_internal.h"
 #include "boac_plain_kernels.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace boac {
 
@@ -73,6 +77,12 @@ __host__ __device__ constexpr size_t fused_tab_floats(int n, int V) {
     // V/4 groups of 4 views or V/2 groups of 2: the same total
     return (size_t)(V / 2) * ((size_t)n * n + (size_t)n);
 }
+// The attenuation exponents one CTA keeps: all grids (G = 1), or in cluster
+// mode the grids of one of G ranks, at most ceil(grids / G).
+__host__ __device__ constexpr size_t fused_tab_floats(int n, int V, bool quad, int G) {
+    return G <= 1 ? fused_tab_floats(n, V)
+                  : (size_t)(((quad ? V / 4 : V / 2) + G - 1) / G) * fused_group_floats(n, quad);
+}
 
 // Whether the images of an n x n candidate live in global memory.
 __host__ __device__ constexpr bool fused_global_images(int n) { return n > 128; }
@@ -88,7 +98,7 @@ __host__ __device__ constexpr size_t fused_smem_bytes(int V) {
     using L = FusedShape<N, NT>;
     return sizeof(float) * ((fused_global_images(N) ? 0 : fused_image_floats<N, NT>()) +
                             4 * L::NSEG * N + 8 * N + 2 * ((V + 1) / 2) * 2) +
-           sizeof(double) * 32;
+           sizeof(double) * 33;
 }
 
 // ---- scatter schedule -------------------------------------------------
@@ -298,12 +308,16 @@ __device__ __forceinline__ void scatter_scheduled(const float* __restrict__ W, f
             const unsigned v = (cur.e[h >> 1] >> (16 * (h & 1))) & 0xFFFFu;
             if (v == kSchedEmpty) continue;
             const int k = (int)(v >> 8), b = (int)(v & 255u);
+            if (!index_ok(k, N) || !index_ok(b, N)) continue;
             float u, w;
             sample_uw(k, b, cs, sn, c, &u, &w);
-            // in (-1, n)^2 by construction: no bounds test
+            // in (-1, n)^2 by construction: no bounds test (checked builds
+            // check the index)
             const float fj = floorf(u), fi = floorf(w);
             const float au = u - fj, aw = w - fi;
-            float* p = img1 + ((int)fi + 1) * P + ((int)fj + 1);
+            const int idx = ((int)fi + 1) * P + ((int)fj + 1);
+            if (!index_ok(idx, (long long)P * (N + 1))) continue;
+            float* p = img1 + idx;
             const float g = W[k * WP + b];
             const float g1 = g * aw, g0 = g - g1;
             const float g01 = g0 * au, g00 = g0 - g01;
@@ -332,8 +346,16 @@ __device__ __forceinline__ const unsigned short* grid_sched(const FusedArgs& a, 
     return a.sched + (size_t)gi * 9 * SchedShape<(N <= 128 ? N : 128)>::CLS_ENTRIES;
 }
 
-template <int N, int NT, bool QUAD>
-__global__ void __launch_bounds__(NT, (fused_min_blocks<N, NT>())) mlem_fused_kernel(FusedArgs a) {
+// G = 1: one CTA per candidate at a time (the batch's iterations split over
+// the CTAs).  G > 1 (cluster mode, for batches too small to fill the GPU one
+// CTA per candidate): a thread-block cluster of G CTAs per candidate, CTA
+// rank r working on the sample grids [r V' / G, (r + 1) V' / G) (V' grids)
+// with its own copy of F and its own accumulator; after every iteration's
+// grids the G accumulators are summed through distributed shared memory,
+// each rank updating its share of the image rows and writing them into
+// every rank's F.
+template <int N, int NT, bool QUAD, int G = 1>
+__global__ void __launch_bounds__(NT, (G > 1 ? 1 : fused_min_blocks<N, NT>())) mlem_fused_kernel(FusedArgs a) {
     using Lay = FusedShape<N, NT>;
     constexpr int P = Lay::P, IMG = Lay::IMG, NN = Lay::NN, WP = Lay::WP;
     constexpr int NSEG = Lay::NSEG, SEG = Lay::SEG;
@@ -370,8 +392,17 @@ __global__ void __launch_bounds__(NT, (fused_min_blocks<N, NT>())) mlem_fused_ke
 
     for (int v = tid; v < V; v += NT) view_cos_sin(v, V, &csn[2 * v], &csn[2 * v + 1]);
 
-    float* tab = a.tab + (size_t)blockIdx.x * fused_tab_floats(N, V);
+    float* tab = a.tab + (size_t)blockIdx.x * fused_tab_floats(N, V, QUAD, G);
     float* sens = a.sens + (size_t)blockIdx.x * NN;
+    // this CTA's sample grids [g0, g1) and (cluster mode) update rows [R0, R1)
+    int rank = 0, g0 = 0, g1 = ngrid, R0 = 0, R1 = N;
+    if constexpr (G > 1) {
+        rank = (int)cg::this_cluster().block_rank();
+        g0 = rank * ngrid / G;
+        g1 = (rank + 1) * ngrid / G;
+        R0 = rank * N / G;
+        R1 = (rank + 1) * N / G;
+    }
 
     __shared__ int wait_ok;
     const long long units = a.job_start ? a.job_start[a.B] : (long long)a.B * (a.K > 0 ? a.K : 1);
@@ -391,7 +422,18 @@ __global__ void __launch_bounds__(NT, (fused_min_blocks<N, NT>())) mlem_fused_ke
     const int j_first = m0 < m1 ? job_of(m0) : 0;
     const int j_last = m0 < m1 ? job_of(m1 - 1) : -1;
 
-    for (int cand = j_last; cand >= j_first; --cand) {
+    // cluster mode: cluster h takes candidates h, h + H, h + 2 H, ... whole
+    const int n_holders = G > 1 ? (int)(gridDim.x / G) : 1;
+    const int holder = G > 1 ? (int)(blockIdx.x / G) : 0;
+    for (int ci = 0;; ++ci) {
+        int cand;
+        if constexpr (G == 1) {
+            cand = j_last - ci;
+            if (cand < j_first) break;
+        } else {
+            cand = holder + ci * n_holders;
+            if (cand >= a.B) break;
+        }
         const RaggedDesc* d = a.desc ? a.desc + cand : nullptr;
         const float* __restrict__ S = a.S + (d ? d->S_off : (long long)cand * a.s_stride);
         const float* __restrict__ mu = a.mu + (d ? d->mu_off : (long long)cand * NN);
@@ -401,7 +443,8 @@ __global__ void __launch_bounds__(NT, (fused_min_blocks<N, NT>())) mlem_fused_ke
         // this CTA's part of the candidate: iterations [it0, it1)
         const long long js = a.job_start ? a.job_start[cand] : (long long)cand * (a.K > 0 ? a.K : 1);
         const long long jl = Kc > 0 ? Kc : 1;
-        const long long u0 = m0 - js > 0 ? m0 - js : 0, u1 = m1 - js < jl ? m1 - js : jl;
+        const long long u0 = G > 1 ? 0 : (m0 - js > 0 ? m0 - js : 0);
+        const long long u1 = G > 1 ? jl : (m1 - js < jl ? m1 - js : jl);
         const bool first = (u0 == 0), last = (u1 == jl);
         const int it0 = (int)(u0 < Kc ? u0 : Kc), it1 = (int)(u1 < Kc ? u1 : Kc);
 
@@ -416,11 +459,11 @@ __global__ void __launch_bounds__(NT, (fused_min_blocks<N, NT>())) mlem_fused_ke
 
         // ---- system matrix (attenuation exponents) + sensitivity A^T 1
         // (loops unrolled by 8, as in the iterations below: +0.8 % measured)
-        for (int gi = 0; gi < ngrid; ++gi) {
+        for (int gi = g0; gi < g1; ++gi) {
             const float cs = csn[2 * gi], sn = csn[2 * gi + 1];
             SchedSlots<SN, NT> sched0;  // this grid's scatter slots of class 0
             if (use_sched) sched0.load(grid_sched<N>(a, gi));
-            float* Xc = tab + gi * gstride;
+            float* Xc = tab + (gi - g0) * gstride;
             float* XrT = Xc + NN;
             float* Uc = QUAD ? Xc + 2 * NN : Xc + NN;
             float* Ur = Uc + N;
@@ -524,10 +567,26 @@ __global__ void __launch_bounds__(NT, (fused_min_blocks<N, NT>())) mlem_fused_ke
             __syncthreads();
             continue;
         }
-        for (int i = tid; i < NN; i += NT) {
-            const int pi = (i / N + 1) * P + (i % N) + 1;
-            sens[i] = img1[pi];
-            img0[pi] = first ? Fc[i] : __ldcg(Fc + i);  // L2: written by another SM
+        if constexpr (G > 1) {
+            // the sensitivity of this rank's rows: the ranks' partial images
+            // summed in rank order
+            cg::cluster_group cl = cg::this_cluster();
+            cl.sync();
+            for (int i = tid; i < (R1 - R0) * N; i += NT) {
+                const int pi = (R0 + i / N + 1) * P + (i % N) + 1;
+                float sv = 0.0f;
+#pragma unroll 1
+                for (int r = 0; r < G; ++r) sv += cl.map_shared_rank(img1, r)[pi];
+                sens[i] = sv;
+            }
+            cl.sync();
+            for (int i = tid; i < NN; i += NT) img0[(i / N + 1) * P + (i % N) + 1] = Fc[i];
+        } else {
+            for (int i = tid; i < NN; i += NT) {
+                const int pi = (i / N + 1) * P + (i % N) + 1;
+                sens[i] = img1[pi];
+                img0[pi] = first ? Fc[i] : __ldcg(Fc + i);  // L2: written by another SM
+            }
         }
         __syncthreads();
         for (int i = tid; i < IMG; i += NT) img1[i] = 0.0f;
@@ -538,17 +597,17 @@ __global__ void __launch_bounds__(NT, (fused_min_blocks<N, NT>())) mlem_fused_ke
         for (int it = it0; it <= it1; ++it) {
             const bool scoring = (it == Kc);
             if (it == it1 && !(last && a.L)) break;
-            for (int gi = 0; gi < ngrid; ++gi) {
+            for (int gi = g0; gi < g1; ++gi) {
                 const float cs = csn[2 * gi], sn = csn[2 * gi + 1];
-                const float* Xc = tab + gi * gstride;
+                const float* Xc = tab + (gi - g0) * gstride;
                 const float* XrT = Xc + NN;
                 const float* Uc = QUAD ? Xc + 2 * NN : Xc + NN;
                 const float* Ur = Uc + N;
                 {   // the next grid's exponent planes are read from DRAM
                     // once per iteration: start that read now (one 128-byte
                     // line per thread, 2 n^2 floats per grid)
-                    const int gn = gi + 1 < ngrid ? gi + 1 : 0;
-                    const float* nxt = tab + gn * gstride;
+                    const int gn = gi + 1 < g1 ? gi + 1 : g0;
+                    const float* nxt = tab + (gn - g0) * gstride;
                     constexpr int kLines = (int)((2 * (size_t)NN * sizeof(float) + 127) / 128);
                     for (int l = tid; l < (QUAD ? kLines : kLines / 2); l += NT) prefetch_l2(nxt + 32 * l);
                 }
@@ -640,16 +699,37 @@ __global__ void __launch_bounds__(NT, (fused_min_blocks<N, NT>())) mlem_fused_ke
                 else scatter_classes<N, NT, P, WP>(W, img1, cs, sn, c);
             }
             if (scoring) break;
-            // multiplicative update; clears the accumulator for the next pass
-            for (int i = tid; i < IMG; i += NT) {
-                const int row = i / P, col = i % P;
-                if (row >= 1 && row <= N && col >= 1 && col <= N) {
-                    const float sv = sens[(row - 1) * N + (col - 1)];
-                    img0[i] = sv > 0.0f ? img0[i] * img1[i] / sv : 0.0f;
+            if constexpr (G > 1) {
+                // this rank's rows: back-projection summed over the ranks in
+                // rank order, multiplicative update, written into every
+                // rank's F; then the accumulator is cleared
+                cg::cluster_group cl = cg::this_cluster();
+                cl.sync();
+                for (int i = tid; i < (R1 - R0) * N; i += NT) {
+                    const int pi = (R0 + i / N + 1) * P + (i % N) + 1;
+                    float bp = 0.0f;
+#pragma unroll 1
+                    for (int r = 0; r < G; ++r) bp += cl.map_shared_rank(img1, r)[pi];
+                    const float sv = sens[i];
+                    const float fn = sv > 0.0f ? img0[pi] * bp / sv : 0.0f;
+#pragma unroll 1
+                    for (int r = 0; r < G; ++r) cl.map_shared_rank(img0, r)[pi] = fn;
                 }
-                img1[i] = 0.0f;
+                cl.sync();
+                for (int i = tid; i < IMG; i += NT) img1[i] = 0.0f;
+                __syncthreads();
+            } else {
+                // multiplicative update; clears the accumulator for the next pass
+                for (int i = tid; i < IMG; i += NT) {
+                    const int row = i / P, col = i % P;
+                    if (row >= 1 && row <= N && col >= 1 && col <= N) {
+                        const float sv = sens[(row - 1) * N + (col - 1)];
+                        img0[i] = sv > 0.0f ? img0[i] * img1[i] / sv : 0.0f;
+                    }
+                    img1[i] = 0.0f;
+                }
+                __syncthreads();
             }
-            __syncthreads();
         }
 
         // ---- Eq. 5: deterministic block reduction of the float64 terms
@@ -660,13 +740,29 @@ __global__ void __launch_bounds__(NT, (fused_min_blocks<N, NT>())) mlem_fused_ke
             if (tid == 0) {
                 double t = 0.0;
                 for (int wi = 0; wi < NT / 32; ++wi) t += dred[wi];
-                a.L[lidx] = a.include_lgamma && a.lgS ? t - *a.lgS : t;
-                if (t == -INFINITY) atomicCAS(a.status, BOAC_OK, BOAC_ENONFINITE);
+                if constexpr (G > 1) {
+                    dred[32] = t;  // this rank's terms
+                } else {
+                    a.L[lidx] = a.include_lgamma && a.lgS ? t - *a.lgS : t;
+                    if (t == -INFINITY) atomicCAS(a.status, BOAC_OK, BOAC_ENONFINITE);
+                }
+            }
+            if constexpr (G > 1) {  // the ranks' terms added in rank order
+                cg::cluster_group cl = cg::this_cluster();
+                cl.sync();
+                if (rank == 0 && tid == 0) {
+                    double t = 0.0;
+                    for (int r = 0; r < G; ++r) t += cl.map_shared_rank(dred, r)[32];
+                    a.L[lidx] = a.include_lgamma && a.lgS ? t - *a.lgS : t;
+                    if (t == -INFINITY) atomicCAS(a.status, BOAC_OK, BOAC_ENONFINITE);
+                }
             }
         }
 
-        // ---- F out (F^K, or the state handed to the candidate's second part)
-        for (int i = tid; i < NN; i += NT) Fc[i] = img0[(i / N + 1) * P + (i % N) + 1];
+        // ---- F out (F^K, or the state handed to the candidate's second part;
+        // cluster mode: each rank its rows)
+        for (int i = R0 * N + tid; i < R1 * N; i += NT) Fc[i] = img0[(i / N + 1) * P + (i % N) + 1];
+        if constexpr (G > 1) cg::this_cluster().sync();  // no rank still reads another's memory
         __syncthreads();
         if (!last && tid == 0 && cand != a.withhold) {
             __threadfence();
@@ -681,19 +777,101 @@ __global__ void __launch_bounds__(NT, (fused_min_blocks<N, NT>())) mlem_fused_ke
 // 2 * shape + (1 for two views per grid).  Ids 6, 7 and 8 are the cluster
 // kernel (boac_band.cu, four views per grid only): 5, 6 or 8 CTAs per
 // candidate for 256 x 256 images, 2, 4 or 8 for 128 x 128.
+// Ids 9 .. 16 are the fused kernel's cluster mode (images up to 128 x 128,
+// four views per grid, CTAs of 8n threads) with 2, 3, 4, 6, 8, 9, 12 or 16
+// CTAs per candidate, each on its share of the sample grids.
 constexpr int kShapes = 3;
 constexpr int kBandConfigs = 3;
-constexpr int kConfigs = 2 * kShapes + kBandConfigs;
+constexpr int kSplitConfigs = 8;
+constexpr int kConfigs = 2 * kShapes + kBandConfigs + kSplitConfigs;
 
 struct FusedVariant {
     int n, nt;
     bool quad;
-    int nb;  // CTAs per candidate: 1, or the cluster size of the band kernel
+    int nb;  // CTAs per candidate in the band kernel's cluster (1 otherwise)
     size_t (*smem)(int V);
     const void* func;
-    // `holders`: CTAs (nb == 1) or clusters that share the work
+    // `holders`: CTAs (nb == 1, g == 1) or clusters that share the work
     int (*launch)(const FusedArgs& a, int holders, cudaStream_t st);
+    int g;   // CTAs per candidate in the fused kernel's cluster mode (1 otherwise)
+    int (*max_clusters)();  // cluster mode: clusters resident at once
 };
+
+// Cluster-mode launches: dynamic shared memory and (16 CTAs) the
+// non-portable cluster size allowed once per device, then the kernel on
+// `clusters` clusters of G CTAs.
+template <int N, int NT, int G>
+static int split_attrs() {
+    constexpr int kDev = 64;
+    static bool done[kDev];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kDev) return launch_status();
+    if (!done[dev]) {
+        if (cudaFuncSetAttribute(mlem_fused_kernel<N, NT, true, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)fused_smem_bytes<N, NT>(kMaxViews)) != cudaSuccess)
+            return launch_status();
+        if (G > 8 && cudaFuncSetAttribute(mlem_fused_kernel<N, NT, true, G>,
+                                          cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+            return launch_status();
+        done[dev] = true;
+    }
+    return BOAC_OK;
+}
+
+template <int N, int NT, int G>
+static cudaLaunchConfig_t split_config(int clusters, int V, cudaStream_t st, cudaLaunchAttribute* attr) {
+    cudaLaunchConfig_t cfg = {};
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = G;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)(clusters * G), 1, 1);
+    cfg.blockDim = dim3(NT, 1, 1);
+    cfg.dynamicSmemBytes = fused_smem_bytes<N, NT>(V);
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+
+template <int N, int NT, int G>
+static int split_max_clusters_t() {
+    constexpr int kDev = 64;
+    static int cached[kDev];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kDev) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (cached[dev]) return cached[dev];
+    if (split_attrs<N, NT, G>() != BOAC_OK) {
+        cudaGetLastError();
+        return 0;
+    }
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = split_config<N, NT, G>(64, kMaxViews, nullptr, attr);
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, mlem_fused_kernel<N, NT, true, G>, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    cached[dev] = n;
+    return n;
+}
+
+template <int N, int NT, int G>
+static int split_launch_t(const FusedArgs& a, int clusters, cudaStream_t st) {
+    int s = split_attrs<N, NT, G>();
+    if (s != BOAC_OK) return s;
+    if (a.sched) {  // the scatter schedule of this geometry, then the kernel
+        s = sched_launch(N, a.V, a.V / 4, const_cast<unsigned short*>(a.sched), st);
+        if (s != BOAC_OK) return s;
+    }
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = split_config<N, NT, G>(clusters, a.V, st, attr);
+    if (cudaLaunchKernelEx(&cfg, mlem_fused_kernel<N, NT, true, G>, a) != cudaSuccess) return launch_status();
+    return launch_status();
+}
 
 template <int N, int NT, bool QUAD>
 static int fused_launch_t(const FusedArgs& a, int slots, cudaStream_t st) {
@@ -724,7 +902,13 @@ static size_t smem_of(int V) { return fused_smem_bytes<N, NT>(V); }
 template <int N, int NT, bool QUAD>
 static FusedVariant make_variant() {
     return FusedVariant{N, NT, QUAD, 1, smem_of<N, NT>, (const void*)mlem_fused_kernel<N, NT, QUAD>,
-                        fused_launch_t<N, NT, QUAD>};
+                        fused_launch_t<N, NT, QUAD>, 1, nullptr};
+}
+
+template <int N, int G>
+static FusedVariant make_split_variant() {
+    return FusedVariant{N, 8 * N, true, 1, smem_of<N, 8 * N>, (const void*)mlem_fused_kernel<N, 8 * N, true, G>,
+                        split_launch_t<N, 8 * N, G>, G, split_max_clusters_t<N, 8 * N, G>};
 }
 
 template <int N, int NB>
@@ -735,7 +919,7 @@ static int band_launch_of(const FusedArgs& a, int clusters, cudaStream_t st) {
 }
 template <int N, int NB>
 static FusedVariant make_band_variant() {
-    return FusedVariant{N, 4 * N, true, NB, band_smem_of<N, NB>, nullptr, band_launch_of<N, NB>};
+    return FusedVariant{N, 4 * N, true, NB, band_smem_of<N, NB>, nullptr, band_launch_of<N, NB>, 1, nullptr};
 }
 
 #define BOAC_SHAPES(NV)                                                                        \
@@ -744,15 +928,24 @@ static FusedVariant make_band_variant() {
         make_variant<NV, (8 * NV > 1024 ? 1024 : 8 * NV), true>(),                             \
         make_variant<NV, (8 * NV > 1024 ? 1024 : 8 * NV), false>()
 #define BOAC_NO_BAND FusedVariant{}, FusedVariant{}, FusedVariant{}
+#define BOAC_SPLIT(NV)                                                                        \
+    make_split_variant<NV, 2>(), make_split_variant<NV, 3>(), make_split_variant<NV, 4>(),  \
+        make_split_variant<NV, 6>(), make_split_variant<NV, 8>(), make_split_variant<NV, 9>(), \
+        make_split_variant<NV, 12>(), make_split_variant<NV, 16>()
+#define BOAC_NO_SPLIT FusedVariant{}, FusedVariant{}, FusedVariant{}, FusedVariant{}, \
+                      FusedVariant{}, FusedVariant{}, FusedVariant{}, FusedVariant{}
 
 static const FusedVariant* variant_table(int n) {
     static const FusedVariant t64[kConfigs] = {BOAC_SHAPES(64), make_band_variant<64, 2>(),
-                                               make_band_variant<64, 4>(), make_band_variant<64, 8>()};
-    static const FusedVariant t96[kConfigs] = {BOAC_SHAPES(96), BOAC_NO_BAND};
+                                               make_band_variant<64, 4>(), make_band_variant<64, 8>(),
+                                               BOAC_SPLIT(64)};
+    static const FusedVariant t96[kConfigs] = {BOAC_SHAPES(96), BOAC_NO_BAND, BOAC_SPLIT(96)};
     static const FusedVariant t128[kConfigs] = {BOAC_SHAPES(128), make_band_variant<128, 2>(),
-                                                make_band_variant<128, 4>(), make_band_variant<128, 8>()};
+                                                make_band_variant<128, 4>(), make_band_variant<128, 8>(),
+                                                BOAC_SPLIT(128)};
     static const FusedVariant t256[kConfigs] = {BOAC_SHAPES(256), make_band_variant<256, 5>(),
-                                                make_band_variant<256, 6>(), make_band_variant<256, 8>()};
+                                                make_band_variant<256, 6>(), make_band_variant<256, 8>(),
+                                                BOAC_NO_SPLIT};
     switch (n) {
         case 64: return t64;
         case 96: return t96;
@@ -770,26 +963,57 @@ static int single_cta_config(const boac_geom* g) {
     return 2 * shape + (g->n_views % 4 == 0 ? 0 : 1);
 }
 
-// Default configuration for B candidates.  256 x 256 images with V % 4 == 0
-// take the cluster kernel with the cluster size that keeps the most SMs
-// busy (clusters are placed within one GPC, so the resident count depends
-// on the size); the smaller cluster on a tie.  128 x 128 images with
-// V % 4 == 0 take the cluster kernel while the batch is too small to occupy
-// the SMs one candidate per CTA: 8 CTAs per candidate for B <= S/4, 4 for
-// B <= 0.45 S (S = SM count; measured on GB300 at 120 views: 1.8x the
-// one-CTA kernel at B = 8, 1.36x at B = 32, +4 % at B = 64, slower from
-// B = 96 on, where every candidate has an SM of its own).
+static const FusedVariant* get_variant(const boac_geom* g, int config);
+
+// Cluster mode for a batch too small to fill the GPU one CTA per candidate
+// (images up to 128 x 128, V % 4 == 0): the cluster size G with the least
+// modelled time, rounds(G) (ceil(grids / G) + 1.6) grid passes per
+// iteration, where rounds(G) = ceil(B / clusters of G resident at once) and
+// 1.6 grid passes stand for the cluster's per-iteration exchange (fitted on
+// GB300 at 128 x 128 and 120 views: 24 us against 15 us per grid pass); the
+// smaller G on a tie; and only if that beats one CTA per candidate, whose
+// even split of the batch's iterations costs grids B / min(B, SMs) passes
+// per iteration.  Returns the configuration id, or -1.
+static int split_config(const boac_geom* g, int B) {
+    if (g->n > 128 || g->n_views % 4 != 0 || B < 1) return -1;
+    const int sms = sm_count();
+    if (sms <= 0) return -1;
+    const int ngrid = g->n_views / 4;
+    int best = -1;
+    double best_t = (double)ngrid * B / (B < sms ? B : sms);  // one CTA per candidate
+    for (int i = 0; i < kSplitConfigs; ++i) {
+        const int cfg = 2 * kShapes + kBandConfigs + i;
+        const FusedVariant* v = get_variant(g, cfg);
+        if (!v) continue;
+        const int h = v->max_clusters();
+        if (h <= 0) continue;
+        const int rounds = (B + h - 1) / h;
+        const double t = rounds * ((ngrid + v->g - 1) / v->g + 1.6);
+        if (t < best_t - 1e-9) {
+            best = cfg;
+            best_t = t;
+        }
+    }
+    return best;
+}
+
+// Default configuration for B candidates.  Batches too small to fill the
+// GPU one candidate per CTA (images up to 128 x 128, V % 4 == 0) take the
+// fused kernel's cluster mode (split_config; measured on GB300 at 128 x 128
+// and K = 20: 1.7x to 2.3x the unfused batched kernels at 1 to 64
+// candidates, 1.2x the one-CTA kernel at 96).  256 x 256 images with
+// V % 4 == 0 take the band kernel with the cluster size that keeps the most
+// SMs busy (clusters are placed within one GPC, so the resident count
+// depends on the size); the smaller cluster on a tie.  Otherwise the one-CTA
+// kernel.
 static int default_config(const boac_geom* g, int B) {
+    const int sc = split_config(g, B);
+    if (sc >= 0) return sc;
     if (g->n == 64 && B >= 1 && B <= 2 * sm_count()) {
         // at most two candidates per SM: CTAs of 8n threads (measured on GB300
         // at 60 views: 1.88 vs 2.16 ms for B = 1 ... 128; from B = 456 on,
         // three 4n-thread CTAs per SM are faster)
         return 2 * 2 + (g->n_views % 4 == 0 ? 0 : 1);
-    }
-    if (g->n == 128 && g->n_views % 4 == 0 && B >= 1) {
-        const int sms = sm_count();
-        if (sms > 0 && 4 * B <= sms && band_max_clusters(128, 8) > 0) return 2 * kShapes + 2;
-        if (sms > 0 && 20 * B <= 9 * sms && band_max_clusters(128, 4) > 0) return 2 * kShapes + 1;
     }
     if (g->n == 256 && g->n_views % 4 == 0) {
         static const int nbs[kBandConfigs] = {5, 6, 8};
@@ -808,12 +1032,14 @@ static int default_config(const boac_geom* g, int B) {
 
 // Batches small enough that the unfused batched kernels (boac_unfused.cu:
 // many CTAs per candidate) finish before the fused kernel's one CTA or one
-// cluster per candidate does.  Measured on GB300 (152 SMs) with K = 20 at
-// 60 / 90 / 120 / 180 views: up to 32 candidates at 64 x 64 and 96 x 96
-// (1.9x / 4.7x at B = 1), 16 at 128 x 128 (2.4x at B = 1), 2 at 256 x 256
-// (1.3x at B = 1); both paths scale with the view count, so the bound is
-// per image size, scaled with the SM count.
+// cluster per candidate does, for the geometries without the cluster mode
+// (view counts not divisible by 4, 256 x 256 images).  Measured on GB300
+// (152 SMs) with K = 20 at 60 / 90 / 120 / 180 views: up to 32 candidates at
+// 64 x 64 and 96 x 96 (1.9x / 4.7x at B = 1), 16 at 128 x 128 (2.4x at
+// B = 1), 2 at 256 x 256 (1.3x at B = 1); both paths scale with the view
+// count, so the bound is per image size, scaled with the SM count.
 static bool use_unfused(const boac_geom* g, int B) {
+    if (split_config(g, B) >= 0) return false;
     int cap;
     switch (g->n) {
         case 64:
@@ -833,6 +1059,7 @@ static const FusedVariant* get_variant(const boac_geom* g, int config) {
     if (!v->launch) return nullptr;
     if (v->quad ? (g->n_views % 4 != 0) : (g->n_views % 2 != 0)) return nullptr;
     if (v->nb > 1 && !band_supported(g->n, g->n_views, v->nb)) return nullptr;
+    if (v->g > 1 && (g->n_views < 4 * v->g)) return nullptr;  // at least one grid per rank
     return v;
 }
 
@@ -882,7 +1109,7 @@ struct FusedLayout {
 
 static FusedLayout fused_layout(const boac_geom* g, const FusedVariant* v, int holders, int B) {
     FusedLayout l;
-    const size_t ctas = (size_t)holders * v->nb;
+    const size_t ctas = (size_t)holders * v->nb * v->g;
     l.status = 0;
     l.tab = 256;
     if (v->nb > 1) {
@@ -891,7 +1118,7 @@ static FusedLayout fused_layout(const boac_geom* g, const FusedVariant* v, int h
         l.geo = l.img + 256;
         l.ready = l.geo + align256(band_geo_bytes(g->n, v->nb, g->n_views));
     } else {
-        l.sens = l.tab + align256(sizeof(float) * ctas * fused_tab_floats(g->n, g->n_views));
+        l.sens = l.tab + align256(sizeof(float) * ctas * fused_tab_floats(g->n, g->n_views, v->quad, v->g));
         l.img = l.sens + align256(sizeof(float) * ctas * g->n * g->n);
         // padded F and accumulator, (n+1)(n+2)+1 floats each, and the
         // n x (n+1) sample buffer, for sides held in global memory
@@ -911,6 +1138,8 @@ static int variant_holders(const boac_geom* g, const FusedVariant* v, int B) {
     long long h;
     if (v->nb > 1) {
         h = band_max_clusters(g->n, v->nb);
+    } else if (v->g > 1) {
+        h = v->max_clusters();
     } else {
         const int per_sm = variant_occupancy(v, g->n_views);
         h = (long long)per_sm * sm_count();
@@ -1045,6 +1274,10 @@ static std::vector<int> ragged_order(const boac_ragged_cand* cands, int B) {
     });
     return order;
 }
+
+#ifdef BOAC_CHECKED
+BOAC_FAULT_READER(bounds_faults_fused)
+#endif
 
 }  // namespace boac
 

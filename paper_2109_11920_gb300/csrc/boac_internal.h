@@ -55,6 +55,14 @@ struct NvtxPhases {
 #define BOAC_NVTX_CAT(a, b) BOAC_NVTX_CAT2(a, b)
 #define BOAC_RANGE(name) ::boac::NvtxRange BOAC_NVTX_CAT(boac_nvtx_, __LINE__)(name)
 
+#ifdef BOAC_CHECKED
+// Checked builds: the bounds-fault counters of the translation units whose
+// kernels gather and scatter through the checked helpers (count, or -1 if
+// the read failed; reset clears the counter).
+int bounds_faults_fused(int reset);
+int bounds_faults_bpgroup(int reset);
+#endif
+
 // Round up to a multiple of 256 bytes.
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
