@@ -145,7 +145,7 @@ def measured_peak_gbs():
 
 def fused_source_hash():
     h = hashlib.sha256()
-    for f in ("boac_fused.cu", "boac_device.cuh"):
+    for f in ("boac_fused.cu", "boac_device.cuh", "boac_sched.cuh"):
         with open(os.path.join(ROOT, "paper_2109_11920_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
