@@ -363,6 +363,17 @@ int boac_score_grad(const boac_geom *g, const boac_tissue *t, const float *c,
                     int B, int include_lgamma, double *L, double *dL_dc,
                     float *F_out, void *ws, size_t ws_bytes, void *stream);
 
+/* boac_score_grad on the batched kernels of every step (one launch per
+ * projection, back-projection and adjoint step), for comparison with the
+ * fused kernel boac_score_grad takes for 64 / 96 / 128 images with a view
+ * count divisible by 4.  Same arguments, results to float rounding, and
+ * workspace (boac_score_grad_workspace_bytes covers both). */
+int boac_score_grad_unfused(const boac_geom *g, const boac_tissue *t,
+                            const float *c, const float *S, long long s_stride,
+                            int K, int ckpt_every, int B, int include_lgamma,
+                            double *L, double *dL_dc, float *F_out, void *ws,
+                            size_t ws_bytes, void *stream);
+
 /* The same score and its gradient in the 9-parameter model (see
  * boac_rasterize_mu_params): p [B][9] float32 (device) in, dL_dp [B][9]
  * float64 (device) out, in the order c_0..c_5, mu_b, mu_c, dR.  Through the

@@ -105,6 +105,7 @@ SIGNATURES = {
                               _P]),
     "boac_score_grad": (_I, [_GP, _TP, _P, _P, _LL, _I, _I, _I, _I, _P, _P, _P, _P, _SZ, _P]),
     "boac_score_grad_params": (_I, [_GP, _P, _P, _LL, _I, _I, _I, _I, _P, _P, _P, _P, _SZ, _P]),
+    "boac_score_grad_unfused": (_I, [_GP, _TP, _P, _P, _LL, _I, _I, _I, _I, _P, _P, _P, _P, _SZ, _P]),
     "boac_sysmat_create": (_I, [_GP, ctypes.POINTER(_P), _P]),
     "boac_sysmat_destroy": (_I, [_P]),
     "boac_sysmat_nnz": (_LL, [_P]),

@@ -212,10 +212,11 @@ def boac_loglik(g: Geom, q: torch.Tensor, S: torch.Tensor, include_lgamma: bool 
 
 def boac_score_grad(g: Geom, t: Tissue, c: torch.Tensor, S: torch.Tensor, K: int,
                     ckpt_every: int = 2, include_lgamma: bool = True, want_image: bool = False,
-                    ws: torch.Tensor | None = None):
+                    ws: torch.Tensor | None = None, unfused: bool = False):
     """Score after K MLEM iterations (AREA map, F^0 = 1) and its gradient with
     respect to the Legendre coefficients: returns (L[B], dL/dc[B, 6], F^K or None),
-    L and dL/dc in float64."""
+    L and dL/dc in float64.  ``unfused=True`` pins the batched launch-per-step
+    kernels (boac_score_grad_unfused) instead of the fused kernel."""
     _need(c, "c", torch.float32)
     if c.dim() != 2 or c.shape[1] != 6:
         raise ValueError("c must be [B, 6]")
@@ -230,7 +231,8 @@ def boac_score_grad(g: Geom, t: Tissue, c: torch.Tensor, S: torch.Tensor, K: int
     L = torch.empty(B, dtype=torch.float64, device=c.device)
     grad = torch.empty(B, 6, dtype=torch.float64, device=c.device)
     F = torch.empty(B, g.n, g.n, dtype=torch.float32, device=c.device) if want_image else None
-    check("boac_score_grad", lib.boac_score_grad(
+    name = "boac_score_grad_unfused" if unfused else "boac_score_grad"
+    check(name, getattr(lib, name)(
         ctypes.byref(g), ctypes.byref(t), _ptr(c), _ptr(S), stride, int(K), int(ckpt_every), B,
         int(include_lgamma), _ptr(L), _ptr(grad), _ptr(F), _ptr(ws), ws.numel(), _stream(c.device)))
     return L, grad, F

@@ -105,6 +105,39 @@ __device__ __forceinline__ double loglik_term(double s, double q, int include_lg
     return t;
 }
 
+// ---- fused score gradient (boac_gradfused.cu): one CTA or a cluster of G
+// CTAs per candidate, 64 / 96 / 128 images, V % 4 == 0.
+struct GradFusedArgs {
+    const float* mu;  // [B][n][n] AREA map
+    const float* S;
+    long long s_stride;
+    int B, V, K, ckpt;
+    float dx;
+    int include_lgamma;
+    const double* lgS;  // shared sinogram: sum of ln S! (or nullptr)
+    float* tab;         // per CTA: exponent planes of its grids
+    float* sens;        // per CTA: n^2 (its rows)
+    float* ck;          // per candidate: [nseg][n^2] F^{j ckpt}
+    float* segF;        // per candidate: [ckpt + 1][n^2] iterates of a segment
+    float* segz;        // per candidate: [ckpt][n^2] z^n = A^T r^n
+    float* segq;        // per candidate: [ckpt][V / 4][4][n] q^n in grid coordinates
+    float* Fbar;        // per candidate: [n^2]
+    float* sensbar;     // per candidate: [n^2]
+    float* abar;        // per candidate: [V][n][n] abar * a, view-ray layout
+    double* L;
+    float* F_out;       // [B][n][n] or nullptr
+    const unsigned short* sched;
+};
+
+bool grad_fused_supported(const boac_geom* g);
+// Cluster size G (1: one CTA per candidate) and the clusters to launch for B
+// candidates; 0 if the fused gradient does not apply.
+int grad_fused_plan(const boac_geom* g, int B, int* holders);
+// Floats of one CTA's exponent slot for cluster size G.
+size_t grad_fused_tab_floats(const boac_geom* g, int G);
+// The scatter schedule of the geometry (into a.sched), then the kernel.
+int grad_fused_launch(const boac_geom* g, const GradFusedArgs& a, int G, int clusters, cudaStream_t st);
+
 // ---- cluster kernel (boac_band.cu): images of side n split into bands of
 // rows over a cluster of nb CTAs per candidate, V % 4 == 0; instantiated for
 // n = 256 with nb in {5, 6, 8} and n = 128 and 64 with nb in {2, 4, 8}.

@@ -26,8 +26,10 @@
 #include <math.h>
 
 #include "boac_device.cuh"
+#include "boac_fused.h"
 #include "boac_internal.h"
 #include "boac_plain_kernels.cuh"
+#include "boac_sched.cuh"
 
 namespace boac {
 
@@ -148,6 +150,21 @@ __global__ void mbar_kernel(int n, int V, float dx, const float* __restrict__ ta
     float prefix = 0.0f;
     for (int k = 0; k < n; ++k) {
         const float aa = ab[(size_t)k * n + b] * __ldg(t + (size_t)k * n + b);
+        ab[(size_t)k * n + b] = -dx * (0.5f * aa + prefix);
+        prefix += aa;
+    }
+}
+
+// The same scan of an abar already multiplied by the factors (the fused
+// gradient kernel accumulates abar * a): mbar_k = -dx (x_k / 2 + sum_{k'<k} x_k').
+__global__ void mbar_scan_kernel(int n, int V, float dx, float* __restrict__ abar) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x, v = blockIdx.y, cand = blockIdx.z;
+    if (b >= n) return;
+    const size_t nn = (size_t)n * n;
+    float* ab = abar + ((size_t)cand * V + v) * nn;
+    float prefix = 0.0f;
+    for (int k = 0; k < n; ++k) {
+        const float aa = ab[(size_t)k * n + b];
         ab[(size_t)k * n + b] = -dx * (0.5f * aa + prefix);
         prefix += aa;
     }
@@ -333,13 +350,117 @@ static GradLayout grad_layout(const boac_geom* g, int B, int K, int ckpt) {
     return L;
 }
 
+// Workspace of the fused gradient (boac_gradfused.cu) with cluster size G on
+// `holders` clusters: per CTA its exponent slot and sensitivity rows; per
+// candidate the AREA map, checkpoints, segment iterates, Fbar, sensbar, the
+// attenuation adjoint and mubar; the grouped back-projection's partials;
+// the ln S! scratch and the scatter schedule.
+struct GradFusedLayout {
+    size_t mu, tab, sens, ck, segF, segz, segq, Fbar, sensbar, abar, mubar, partial, lg, sched, total;
+};
+
+static GradFusedLayout grad_fused_layout(const boac_geom* g, int B, int K, int ckpt, int G, int holders) {
+    const size_t nn = (size_t)g->n * g->n, vb = (size_t)g->n_views * g->n_bins;
+    const size_t Bs = (size_t)B, ctas = (size_t)holders * G;
+    const int nseg = (K + ckpt - 1) / ckpt;
+    GradFusedLayout L{};
+    size_t off = 0;
+    auto take = [&](size_t floats) {
+        size_t o = off;
+        off += align256(floats * sizeof(float));
+        return o;
+    };
+    L.mu = take(Bs * nn);
+    L.tab = take(ctas * grad_fused_tab_floats(g, G));
+    L.sens = take(ctas * nn);
+    L.ck = take(Bs * (size_t)(nseg > 0 ? nseg : 1) * nn);
+    L.segF = take(Bs * (size_t)(ckpt + 1) * nn);
+    L.segz = take(Bs * (size_t)ckpt * nn);
+    L.segq = take(Bs * (size_t)ckpt * vb);
+    L.Fbar = take(Bs * nn);
+    L.sensbar = take(Bs * nn);
+    L.abar = take(Bs * g->n_views * nn);
+    L.mubar = take(Bs * nn);
+    L.partial = take(bp_partial_floats(g, B));
+    L.lg = take(2 * kLgammaScratchDoubles);
+    L.sched = off;
+    off += sched_bytes(g->n, g->n_views / 4);
+    L.total = off;
+    return L;
+}
+
+// The fused path: rasterise (AREA), the fused kernel, then mbar scan ->
+// pixels -> coefficients.
+static int score_grad_fused_run(const boac_geom* g, const boac_tissue* t, const float* c, const float* S,
+                                long long s_stride, int K, int ckpt, int B, int include_lgamma, double* L,
+                                double* dL_dc, float* F_out, void* ws, size_t ws_bytes, cudaStream_t st, int G,
+                                int holders) {
+    const GradFusedLayout lay = grad_fused_layout(g, B, K, ckpt, G, holders);
+    if (!ws || ws_bytes < lay.total) return BOAC_EWORKSPACE;
+    char* base = static_cast<char*>(ws);
+    auto P = [&](size_t off) { return reinterpret_cast<float*>(base + off); };
+    const int n = g->n, V = g->n_views;
+    const float dx = g->pixel_cm;
+    const size_t vb = (size_t)V * g->n_bins;
+    NvtxPhases phase("gradient (fused): rasterise");
+    int s = rasterize_launch(g, t, c, t ? 6 : kParams, B, BOAC_RASTER_AREA, P(lay.mu), st);
+    if (s != BOAC_OK) return s;
+    GradFusedArgs a;
+    a.mu = P(lay.mu);
+    a.S = S;
+    a.s_stride = s_stride;
+    a.B = B;
+    a.V = V;
+    a.K = K;
+    a.ckpt = ckpt;
+    a.dx = dx;
+    a.include_lgamma = include_lgamma;
+    a.lgS = include_lgamma && s_stride == 0
+                ? lgamma_sum((int)vb, S, reinterpret_cast<double*>(base + lay.lg), st)
+                : nullptr;
+    a.tab = P(lay.tab);
+    a.sens = P(lay.sens);
+    a.ck = P(lay.ck);
+    a.segF = P(lay.segF);
+    a.segz = P(lay.segz);
+    a.segq = P(lay.segq);
+    a.Fbar = P(lay.Fbar);
+    a.sensbar = P(lay.sensbar);
+    a.abar = P(lay.abar);
+    a.L = L;
+    a.F_out = F_out;
+    a.sched = reinterpret_cast<const unsigned short*>(base + lay.sched);
+    phase.next("gradient (fused): forward, score, reverse sweep");
+    s = grad_fused_launch(g, a, G, holders, st);
+    if (s != BOAC_OK) return s;
+    phase.next("gradient (fused): mu samples -> pixels -> coefficients");
+    mbar_scan_kernel<<<ray_grid(g, B), kRayThreads, 0, st>>>(n, V, dx, P(lay.abar));
+    backproject_table(g, B, P(lay.abar), nullptr, 1.0f, P(lay.mubar), 0, P(lay.partial), st);
+    if (t)
+        grad_coef_kernel<6><<<B, 256, 0, st>>>(n, (double)dx, (double)t->mu_b, (double)t->mu_c, (double)t->dR, c,
+                                               P(lay.mubar), dL_dc);
+    else
+        grad_coef_kernel<kParams><<<B, 256, 0, st>>>(n, (double)dx, 0.0, 0.0, 0.0, c, P(lay.mubar), dL_dc);
+    return launch_status();
+}
+
+// The path boac_score_grad takes: the fused kernel where it applies (G > 0).
+static int grad_plan(const boac_geom* g, int B, int* holders) {
+    *holders = 0;
+    return grad_fused_plan(g, B, holders);
+}
+
 }  // namespace boac
 
 using namespace boac;
 
 extern "C" size_t boac_score_grad_workspace_bytes(const boac_geom* g, int B, int K, int ckpt_every) {
     if (!geom_ok(g) || B < 1 || B > 65535 || K < 0 || ckpt_every < 1) return 0;
-    return grad_layout(g, B, K, ckpt_every).total;
+    int holders = 0;
+    const int G = grad_plan(g, B, &holders);
+    const size_t fused = G > 0 ? grad_fused_layout(g, B, K, ckpt_every, G, holders).total : 0;
+    const size_t unfused = grad_layout(g, B, K, ckpt_every).total;
+    return fused > unfused ? fused : unfused;
 }
 
 // Score and gradient of B candidates: t != nullptr takes c[B][6] with the
@@ -348,7 +469,14 @@ extern "C" size_t boac_score_grad_workspace_bytes(const boac_geom* g, int B, int
 static int score_grad_run(const boac_geom* g, const boac_tissue* t, const float* c,
                           const float* S, long long s_stride, int K, int ckpt_every, int B,
                           int include_lgamma, double* L, double* dL_dc, float* F_out, void* ws,
-                          size_t ws_bytes, void* stream) {
+                          size_t ws_bytes, void* stream, bool allow_fused = true) {
+    if (allow_fused) {
+        int holders = 0;
+        const int G = grad_plan(g, B, &holders);
+        if (G > 0)
+            return score_grad_fused_run(g, t, c, S, s_stride, K, ckpt_every, B, include_lgamma, L, dL_dc, F_out,
+                                        ws, ws_bytes, as_stream(stream), G, holders);
+    }
     const GradLayout lay = grad_layout(g, B, K, ckpt_every);
     if (!ws || ws_bytes < lay.total) return BOAC_EWORKSPACE;
     char* base = static_cast<char*>(ws);
@@ -464,6 +592,18 @@ extern "C" int boac_score_grad(const boac_geom* g, const boac_tissue* t, const f
         return BOAC_EINVAL;
     return score_grad_run(g, t, c, S, s_stride, K, ckpt_every, B, include_lgamma, L, dL_dc, F_out,
                           ws, ws_bytes, stream);
+}
+
+extern "C" int boac_score_grad_unfused(const boac_geom* g, const boac_tissue* t, const float* c,
+                                       const float* S, long long s_stride, int K, int ckpt_every, int B,
+                                       int include_lgamma, double* L, double* dL_dc, float* F_out, void* ws,
+                                       size_t ws_bytes, void* stream) {
+    BOAC_RANGE("boac_score_grad_unfused");
+    if (!geom_ok(g) || !t || !c || !S || !L || !dL_dc || B < 1 || B > 65535 || K < 0 ||
+        ckpt_every < 1 || s_stride < 0 || !(t->dR >= 0.0f))
+        return BOAC_EINVAL;
+    return score_grad_run(g, t, c, S, s_stride, K, ckpt_every, B, include_lgamma, L, dL_dc, F_out,
+                          ws, ws_bytes, stream, false);
 }
 
 extern "C" int boac_score_grad_params(const boac_geom* g, const float* p, const float* S,

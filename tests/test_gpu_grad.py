@@ -14,11 +14,11 @@ from problems import make_problem
 pytestmark = pytest.mark.gpu
 
 
-def run_grad(p, dev, K, ckpt, coefs=None, per_cand_S=None):
+def run_grad(p, dev, K, ckpt, coefs=None, per_cand_S=None, unfused=False):
     c = torch.tensor(p.coefs if coefs is None else coefs, dtype=torch.float32, device=dev)
     S = torch.tensor(p.S if per_cand_S is None else per_cand_S, dtype=torch.float32, device=dev)
     L, grad, F = boac.boac_score_grad(Geom.make(p.n, p.dx, p.V), Tissue(*p.tissue), c, S, K,
-                                      ckpt_every=ckpt, want_image=True)
+                                      ckpt_every=ckpt, want_image=True, unfused=unfused)
     return L.cpu().numpy(), grad.cpu().numpy(), F.cpu().numpy()
 
 
@@ -91,3 +91,21 @@ def test_autograd_function(cuda):
     (L * w).sum().backward()
     _, grad, _ = boac.boac_score_grad(g, t, c.detach(), S, 3, 2)
     torch.testing.assert_close(c.grad, (w[:, None] * grad).float())
+
+
+@pytest.mark.parametrize("shape", [(64, 0.4, 60), (96, 25.6 / 96, 90), (128, 0.2, 120)])
+def test_fused_gradient_against_oracle_and_unfused(cuda, shape):
+    """The fused kernel (boac_score_grad's path at these sizes: one CTA or a
+    cluster per candidate) against the FP64 oracle adjoint and against the
+    batched launch-per-step kernels, with a checkpoint interval that does
+    not divide K (a short last segment)."""
+    n, dx, V = shape
+    p = make_problem(n, dx, V, 2e5, B=5, seed=44, mode=oracle.AREA)
+    K = 5
+    L, grad, F = run_grad(p, cuda, K, ckpt=2)
+    Lu, gu, Fu = run_grad(p, cuda, K, ckpt=2, unfused=True)
+    check_against_oracle(p, L, grad, F, K, [0, 4])
+    np.testing.assert_allclose(L, Lu, rtol=1e-7)
+    for b in range(5):
+        np.testing.assert_allclose(grad[b], gu[b], rtol=2e-4, atol=2e-4 * np.abs(gu[b]).max())
+    assert np.linalg.norm(F - Fu) / np.linalg.norm(Fu) < 1e-5
