@@ -352,11 +352,13 @@ static GradLayout grad_layout(const boac_geom* g, int B, int K, int ckpt) {
 
 // Workspace of the fused gradient (boac_gradfused.cu) with cluster size G on
 // `holders` clusters: per CTA its exponent slot and sensitivity rows; per
-// candidate the AREA map, checkpoints, segment iterates, Fbar, sensbar, the
-// attenuation adjoint and mubar; the grouped back-projection's partials;
+// candidate the AREA map, checkpoints, segment iterates (with their samples
+// on every grid, two layouts), Fbar, sensbar, the attenuation adjoint and
+// mubar; the grouped back-projection's partials;
 // the ln S! scratch and the scatter schedule.
 struct GradFusedLayout {
-    size_t mu, tab, sens, ck, segF, segz, segq, Fbar, sensbar, abar, mubar, partial, lg, sched, total;
+    size_t mu, tab, sens, ck, segF, segz, segq, segB, segBT, Fbar, sensbar, abar, mubar, partial, lg, sched,
+        total;
 };
 
 static GradFusedLayout grad_fused_layout(const boac_geom* g, int B, int K, int ckpt, int G, int holders) {
@@ -377,6 +379,8 @@ static GradFusedLayout grad_fused_layout(const boac_geom* g, int B, int K, int c
     L.segF = take(Bs * (size_t)(ckpt + 1) * nn);
     L.segz = take(Bs * (size_t)ckpt * nn);
     L.segq = take(Bs * (size_t)ckpt * vb);
+    L.segB = take(Bs * (size_t)ckpt * (g->n_views / 4) * nn);
+    L.segBT = take(Bs * (size_t)ckpt * (g->n_views / 4) * nn);
     L.Fbar = take(Bs * nn);
     L.sensbar = take(Bs * nn);
     L.abar = take(Bs * g->n_views * nn);
@@ -424,6 +428,8 @@ static int score_grad_fused_run(const boac_geom* g, const boac_tissue* t, const 
     a.segF = P(lay.segF);
     a.segz = P(lay.segz);
     a.segq = P(lay.segq);
+    a.segB = P(lay.segB);
+    a.segBT = P(lay.segBT);
     a.Fbar = P(lay.Fbar);
     a.sensbar = P(lay.sensbar);
     a.abar = P(lay.abar);

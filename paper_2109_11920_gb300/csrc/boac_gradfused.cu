@@ -64,24 +64,6 @@ __host__ __device__ constexpr size_t grad_fused_smem_bytes(int V) {
            sizeof(double) * 33;
 }
 
-// Bilinear sample of an unpadded image in global memory written earlier by
-// this kernel (read through L2, not the read-only path).
-__device__ __forceinline__ float bilerp_cg(const float* img, int n, float u, float w) {
-    if (!inside_open(u, w, n)) return 0.0f;
-    float fj = floorf(u), fi = floorf(w);
-    float au = u - fj, aw = w - fi;
-    int j0 = (int)fj, i0 = (int)fi;
-    float v00 = 0.f, v01 = 0.f, v10 = 0.f, v11 = 0.f;
-    bool jl = j0 >= 0, jh = j0 + 1 < n, il = i0 >= 0, ih = i0 + 1 < n;
-    if (il && jl) v00 = __ldcg(img + i0 * n + j0);
-    if (il && jh) v01 = __ldcg(img + i0 * n + j0 + 1);
-    if (ih && jl) v10 = __ldcg(img + (i0 + 1) * n + j0);
-    if (ih && jh) v11 = __ldcg(img + (i0 + 1) * n + j0 + 1);
-    float top = fmaf(au, v01 - v00, v00);
-    float bot = fmaf(au, v11 - v10, v10);
-    return fmaf(aw, bot - top, top);
-}
-
 template <int N, int G>
 __global__ void __launch_bounds__(8 * N, 1) grad_fused_kernel(GradFusedArgs a) {
     using Sh = GradShape<N>;
@@ -163,7 +145,7 @@ __global__ void __launch_bounds__(8 * N, 1) grad_fused_kernel(GradFusedArgs a) {
     // sample for views phi, phi + pi (columns) and phi +- pi/2 (rows), in grid
     // coordinates.  Also stages the grid's sinogram rows into Sg (by grid
     // coordinate: S of view phi + pi and phi + 3pi/2 reversed).
-    auto project_grid = [&](int gi, const float* S) {
+    auto project_grid = [&](int gi, const float* S, float* bf, float* bft) {
         const float cs = csn[2 * gi], sn = csn[2 * gi + 1];
         const float* Xc = tab + (gi - g0) * gstride;
         const float* XrT = Xc + NN;
@@ -184,6 +166,7 @@ __global__ void __launch_bounds__(8 * N, 1) grad_fused_kernel(GradFusedArgs a) {
                 sample_uw(k, lb, cs, sn, c, &u, &w);
                 const float f = bilerp_padded(img0, P, N, u, w);
                 W[k * WP + lb] = f;
+                if (bf) bf[k * N + lb] = f;
                 const float y = Xc[k * N + lb];
                 acc1 = fmaf(ex2(y), f, acc1);
                 acc2 = fmaf(ex2(uc - y), f, acc2);
@@ -199,6 +182,7 @@ __global__ void __launch_bounds__(8 * N, 1) grad_fused_kernel(GradFusedArgs a) {
             for (int s = 0; s < SEG; ++s) {
                 const int b = k0 + s;
                 const float f = W[lb * WP + b];
+                if (bft) bft[b * N + lb] = f;
                 const float y = XrT[b * N + lb];
                 acc3 = fmaf(ex2(y), f, acc3);
                 acc4 = fmaf(ex2(ur - y), f, acc4);
@@ -218,12 +202,13 @@ __global__ void __launch_bounds__(8 * N, 1) grad_fused_kernel(GradFusedArgs a) {
         __syncthreads();
     };
     // abar_v(sample) += a_v dx (k1_v x + k2_v y): x the samples in W, y the
-    // samples of the unpadded global image Y (nullptr: none), k1 / k2 per
-    // ray in grid coordinates (k2 unused without Y); view-ray layout of
+    // samples stored by an earlier project_grid of another image (Yc: by
+    // sample (k, b) at k n + b, Yr: at b n + k; nullptr: none), k1 / k2 per
+    // ray in grid coordinates (k2 unused without y); view-ray layout of
     // abar: view phi sample (k, b) at (k, b), phi + pi at (n-1-k, n-1-b),
     // phi + pi/2 at (n-1-b, k), phi + 3pi/2 at (b, n-1-k).  Reads W only.
-    auto abar_grid = [&](int gi, float* ab, const float* k1, const float* k2, const float* Y) {
-        const float cs = csn[2 * gi], sn = csn[2 * gi + 1];
+    auto abar_grid = [&](int gi, float* ab, const float* k1, const float* k2, const float* Yc, const float* Yr) {
+        const bool Y = Yc != nullptr;
         const float* Xc = tab + (gi - g0) * gstride;
         const float* XrT = Xc + NN;
         const float* Uc = Xc + 2 * NN;
@@ -234,15 +219,11 @@ __global__ void __launch_bounds__(8 * N, 1) grad_fused_kernel(GradFusedArgs a) {
             const float uc = Uc[lb];
             const float w11 = dx * k1[lb], w12 = dx * k1[N + lb];
             const float w21 = Y ? dx * k2[lb] : 0.0f, w22 = Y ? dx * k2[N + lb] : 0.0f;
+#pragma unroll 4
             for (int s = 0; s < SEG; ++s) {
                 const int k = k0 + s;
                 const float x = W[k * WP + lb];
-                float yv = 0.0f;
-                if (Y) {
-                    float u, w;
-                    sample_uw(k, lb, cs, sn, c, &u, &w);
-                    yv = bilerp_cg(Y, N, u, w);
-                }
+                const float yv = Y ? __ldcg(Yc + k * N + lb) : 0.0f;
                 const float ye = Xc[k * N + lb];
                 const size_t i1 = (size_t)k * N + lb, i2 = (size_t)(N - 1 - k) * N + (N - 1 - lb);
                 a1[i1] = __ldcg(a1 + i1) + ex2(ye) * fmaf(w21, yv, w11 * x);
@@ -256,15 +237,11 @@ __global__ void __launch_bounds__(8 * N, 1) grad_fused_kernel(GradFusedArgs a) {
             const float ur = Ur[k];
             const float w13 = dx * k1[2 * N + k], w14 = dx * k1[3 * N + k];
             const float w23 = Y ? dx * k2[2 * N + k] : 0.0f, w24 = Y ? dx * k2[3 * N + k] : 0.0f;
+#pragma unroll 4
             for (int s = 0; s < SEG; ++s) {
                 const int b = k0 + s;
                 const float x = W[k * WP + b];
-                float yv = 0.0f;
-                if (Y) {
-                    float u, w;
-                    sample_uw(k, b, cs, sn, c, &u, &w);
-                    yv = bilerp_cg(Y, N, u, w);
-                }
+                const float yv = Y ? __ldcg(Yr + b * N + k) : 0.0f;
                 const float ye = XrT[b * N + k];
                 const size_t i3 = (size_t)(N - 1 - b) * N + k, i4 = (size_t)b * N + (N - 1 - k);
                 a3[i3] = __ldcg(a3 + i3) + ex2(ye) * fmaf(w23, yv, w13 * x);
@@ -318,6 +295,8 @@ __global__ void __launch_bounds__(8 * N, 1) grad_fused_kernel(GradFusedArgs a) {
         float* Fbar = a.Fbar + (size_t)cand * NN;
         float* sensbar = a.sensbar + (size_t)cand * NN;
         float* ab = a.abar + (size_t)cand * V * NN;
+        float* segB = a.segB + (size_t)cand * a.ckpt * ngrid * NN;
+        float* segBT = a.segBT + (size_t)cand * a.ckpt * ngrid * NN;
 
         // ---- 1. set-up: mu -> img0, exponents of this rank's grids, sens
         for (int i = tid; i < IMG; i += NT) {
@@ -412,7 +391,9 @@ __global__ void __launch_bounds__(8 * N, 1) grad_fused_kernel(GradFusedArgs a) {
             if (rec)
                 for (int i = R0 * N + tid; i < R1 * N; i += NT) segF[(size_t)t * NN + i] = img0[pad(i)];
             for (int gi = g0; gi < g1; ++gi) {
-                project_grid(gi, S);
+                // (rec: the samples of F^n too, for the reverse step's abar)
+                project_grid(gi, S, rec ? segB + ((size_t)t * ngrid + gi) * NN : nullptr,
+                             rec ? segBT + ((size_t)t * ngrid + gi) * NN : nullptr);
                 for (int u = tid; u < 4 * N; u += NT) {
                     const float q = qv[u];
                     if (rec) segq[((size_t)t * ngrid + gi) * 4 * N + u] = q;
@@ -443,14 +424,14 @@ __global__ void __launch_bounds__(8 * N, 1) grad_fused_kernel(GradFusedArgs a) {
         // ---- 3. score at F^K and its adjoint
         double lacc = 0.0;
         for (int gi = g0; gi < g1; ++gi) {
-            project_grid(gi, S);
+            project_grid(gi, S, nullptr, nullptr);
             for (int u = tid; u < 4 * N; u += NT) {
                 const float s = Sg[u], q = qv[u];
                 lacc += loglik_term(s, q, a.include_lgamma && !a.lgS);
                 c1[u] = s > 0.0f ? (q > 0.0f ? s / q - 1.0f : 0.0f) : -1.0f;
             }
             __syncthreads();
-            abar_grid(gi, ab, c1, nullptr, nullptr);  // W holds B F^K
+            abar_grid(gi, ab, c1, nullptr, nullptr, nullptr);  // W holds B F^K
             backproject_grid(gi, c1);
         }
         for (int off = 16; off > 0; off >>= 1) lacc += __shfl_down_sync(0xffffffffu, lacc, off);
@@ -508,14 +489,15 @@ __global__ void __launch_bounds__(8 * N, 1) grad_fused_kernel(GradFusedArgs a) {
                 }
                 cluster_sync();
                 for (int gi = g0; gi < g1; ++gi) {
-                    project_grid(gi, S);  // W <- B zbar, qv <- A zbar (rbar)
+                    project_grid(gi, S, nullptr, nullptr);  // W <- B zbar, qv <- A zbar (rbar)
                     for (int u = tid; u < 4 * N; u += NT) {
                         const float q = __ldcg(segq + ((size_t)t * ngrid + gi) * 4 * N + u), s = Sg[u];
                         c1[u] = q > 0.0f ? s / q : 0.0f;                       // r^n
                         c2[u] = q > 0.0f ? -qv[u] * (s / (q * q)) : 0.0f;      // qbar'
                     }
                     __syncthreads();
-                    abar_grid(gi, ab, c1, c2, Fn);
+                    abar_grid(gi, ab, c1, c2, segB + ((size_t)t * ngrid + gi) * NN,
+                              segBT + ((size_t)t * ngrid + gi) * NN);  // y = B F^n
                     backproject_grid(gi, c2);
                 }
                 cluster_sync();
@@ -532,8 +514,8 @@ __global__ void __launch_bounds__(8 * N, 1) grad_fused_kernel(GradFusedArgs a) {
         for (int t = tid; t < 4 * N; t += NT) c1[t] = 1.0f;
         __syncthreads();
         for (int gi = g0; gi < g1; ++gi) {
-            project_grid(gi, S);  // W <- B sensbar
-            abar_grid(gi, ab, c1, nullptr, nullptr);
+            project_grid(gi, S, nullptr, nullptr);  // W <- B sensbar
+            abar_grid(gi, ab, c1, nullptr, nullptr, nullptr);
         }
         cluster_sync();  // no rank still reads another's memory
     }
