@@ -15,7 +15,8 @@
 //      q = 0 < S, -1 where S = 0), Fbar = A^T qbar, and the adjoint of every
 //      attenuation factor, abar += dx qbar (B F^K);
 //   4. the reverse sweep, one checkpoint segment at a time (last first):
-//      recompute the segment's iterates F^n, q^n, z^n = A^T r^n, then for
+//      recompute the segment's iterates F^n, q^n, z^n = A^T r^n (the last
+//      segment keeps them from the forward pass), then for
 //      n from the segment's end down to its start
 //        zbar = Fbar F^n / sens,  sensbar -= Fbar F^{n+1} / sens,
 //        rbar = A zbar,  qbar' = -rbar S / (q^n)^2 (0 where q^n = 0),
@@ -47,6 +48,14 @@
 namespace cg = cooperative_groups;
 
 namespace boac {
+
+// x += v at L2 without waiting for the old value (red.global.add).  Every
+// element of abar is updated by one thread per pass, and one thread's
+// updates of an address are applied in program order, so the sums are those
+// of a read-modify-write, bit for bit.
+__device__ __forceinline__ void red_add(float* p, float v) {
+    asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
 
 template <int N>
 struct GradShape {
@@ -206,7 +215,8 @@ __global__ void __launch_bounds__(8 * N, 1) grad_fused_kernel(GradFusedArgs a) {
     // sample (k, b) at k n + b, Yr: at b n + k; nullptr: none), k1 / k2 per
     // ray in grid coordinates (k2 unused without y); view-ray layout of
     // abar: view phi sample (k, b) at (k, b), phi + pi at (n-1-k, n-1-b),
-    // phi + pi/2 at (n-1-b, k), phi + 3pi/2 at (b, n-1-k).  Reads W only.
+    // phi + pi/2 at (n-1-b, k), phi + 3pi/2 at (b, n-1-k).  Reads W only;
+    // the additions are fire-and-forget reductions at L2.
     auto abar_grid = [&](int gi, float* ab, const float* k1, const float* k2, const float* Yc, const float* Yr) {
         const bool Y = Yc != nullptr;
         const float* Xc = tab + (gi - g0) * gstride;
@@ -226,8 +236,8 @@ __global__ void __launch_bounds__(8 * N, 1) grad_fused_kernel(GradFusedArgs a) {
                 const float yv = Y ? __ldcg(Yc + k * N + lb) : 0.0f;
                 const float ye = Xc[k * N + lb];
                 const size_t i1 = (size_t)k * N + lb, i2 = (size_t)(N - 1 - k) * N + (N - 1 - lb);
-                a1[i1] = __ldcg(a1 + i1) + ex2(ye) * fmaf(w21, yv, w11 * x);
-                a2[i2] = __ldcg(a2 + i2) + ex2(uc - ye) * fmaf(w22, yv, w12 * x);
+                red_add(a1 + i1, ex2(ye) * fmaf(w21, yv, w11 * x));
+                red_add(a2 + i2, ex2(uc - ye) * fmaf(w22, yv, w12 * x));
             }
         }
         {   // row views, thread on row lb
@@ -244,8 +254,8 @@ __global__ void __launch_bounds__(8 * N, 1) grad_fused_kernel(GradFusedArgs a) {
                 const float yv = Y ? __ldcg(Yr + b * N + k) : 0.0f;
                 const float ye = XrT[b * N + k];
                 const size_t i3 = (size_t)(N - 1 - b) * N + k, i4 = (size_t)b * N + (N - 1 - k);
-                a3[i3] = __ldcg(a3 + i3) + ex2(ye) * fmaf(w23, yv, w13 * x);
-                a4[i4] = __ldcg(a4 + i4) + ex2(ur - ye) * fmaf(w24, yv, w14 * x);
+                red_add(a3 + i3, ex2(ye) * fmaf(w23, yv, w13 * x));
+                red_add(a4 + i4, ex2(ur - ye) * fmaf(w24, yv, w14 * x));
             }
         }
         __syncthreads();
@@ -414,11 +424,14 @@ __global__ void __launch_bounds__(8 * N, 1) grad_fused_kernel(GradFusedArgs a) {
             __syncthreads();
         };
 
-        // ---- 2. forward with checkpoints
+        // ---- 2. forward with checkpoints; the iterations of the last
+        // segment keep their data for the reverse sweep as they run, so that
+        // segment is not recomputed
+        const int n_last = nseg > 0 ? (nseg - 1) * a.ckpt : 0;
         for (int it = 0; it < a.K; ++it) {
             if (it % a.ckpt == 0)
                 for (int i = R0 * N + tid; i < R1 * N; i += NT) ck[(size_t)(it / a.ckpt) * NN + i] = img0[pad(i)];
-            mlem_iteration(false, 0);
+            mlem_iteration(it >= n_last, it - n_last);
         }
 
         // ---- 3. score at F^K and its adjoint
@@ -464,10 +477,12 @@ __global__ void __launch_bounds__(8 * N, 1) grad_fused_kernel(GradFusedArgs a) {
         for (int j = nseg - 1; j >= 0; --j) {
             const int n0 = j * a.ckpt;
             const int len = a.K - n0 < a.ckpt ? a.K - n0 : a.ckpt;
-            // recompute: F^{n0} from its checkpoint into every rank's img0
-            for (int i = R0 * N + tid; i < R1 * N; i += NT) put_all(pad(i), __ldcg(ck + (size_t)j * NN + i));
-            cluster_sync();
-            for (int t = 0; t < len; ++t) mlem_iteration(true, t);
+            if (j < nseg - 1) {  // recompute: F^{n0} from its checkpoint into every rank's img0
+                for (int i = R0 * N + tid; i < R1 * N; i += NT) put_all(pad(i), __ldcg(ck + (size_t)j * NN + i));
+                cluster_sync();
+                for (int t = 0; t < len; ++t) mlem_iteration(true, t);
+            }
+            // F^{n0 + len} (the last segment: F^K, still in img0)
             for (int i = R0 * N + tid; i < R1 * N; i += NT) segF[(size_t)len * NN + i] = img0[pad(i)];
             cluster_sync();
             for (int t = len - 1; t >= 0; --t) {
