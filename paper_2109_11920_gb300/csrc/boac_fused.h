@@ -125,7 +125,8 @@ struct GradFusedArgs {
     float* segBT;       // the same samples at [b][k] (row-wise reads)
     float* Fbar;        // per candidate: [n^2]
     float* sensbar;     // per candidate: [n^2]
-    float* abar;        // per candidate: [V][n][n] abar * a, view-ray layout
+    float* abar;        // per candidate: [V / 4][n][n] adjoint of the mu samples of each grid
+    float* mubar;       // per candidate: [n^2] adjoint of the pixels of mu
     double* L;
     float* F_out;       // [B][n][n] or nullptr
     const unsigned short* sched;

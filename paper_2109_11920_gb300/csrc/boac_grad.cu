@@ -357,8 +357,7 @@ static GradLayout grad_layout(const boac_geom* g, int B, int K, int ckpt) {
 // mubar; the grouped back-projection's partials;
 // the ln S! scratch and the scatter schedule.
 struct GradFusedLayout {
-    size_t mu, tab, sens, ck, segF, segz, segq, segB, segBT, Fbar, sensbar, abar, mubar, partial, lg, sched,
-        total;
+    size_t mu, tab, sens, ck, segF, segz, segq, segB, segBT, Fbar, sensbar, abar, mubar, lg, sched, total;
 };
 
 static GradFusedLayout grad_fused_layout(const boac_geom* g, int B, int K, int ckpt, int G, int holders) {
@@ -383,9 +382,8 @@ static GradFusedLayout grad_fused_layout(const boac_geom* g, int B, int K, int c
     L.segBT = take(Bs * (size_t)ckpt * (g->n_views / 4) * nn);
     L.Fbar = take(Bs * nn);
     L.sensbar = take(Bs * nn);
-    L.abar = take(Bs * g->n_views * nn);
+    L.abar = take(Bs * (size_t)(g->n_views / 4) * nn);
     L.mubar = take(Bs * nn);
-    L.partial = take(bp_partial_floats(g, B));
     L.lg = take(2 * kLgammaScratchDoubles);
     L.sched = off;
     off += sched_bytes(g->n, g->n_views / 4);
@@ -393,8 +391,8 @@ static GradFusedLayout grad_fused_layout(const boac_geom* g, int B, int K, int c
     return L;
 }
 
-// The fused path: rasterise (AREA), the fused kernel, then mbar scan ->
-// pixels -> coefficients.
+// The fused path: rasterise (AREA), the fused kernel (through mubar), then
+// the coefficients.
 static int score_grad_fused_run(const boac_geom* g, const boac_tissue* t, const float* c, const float* S,
                                 long long s_stride, int K, int ckpt, int B, int include_lgamma, double* L,
                                 double* dL_dc, float* F_out, void* ws, size_t ws_bytes, cudaStream_t st, int G,
@@ -433,15 +431,14 @@ static int score_grad_fused_run(const boac_geom* g, const boac_tissue* t, const 
     a.Fbar = P(lay.Fbar);
     a.sensbar = P(lay.sensbar);
     a.abar = P(lay.abar);
+    a.mubar = P(lay.mubar);
     a.L = L;
     a.F_out = F_out;
     a.sched = reinterpret_cast<const unsigned short*>(base + lay.sched);
     phase.next("gradient (fused): forward, score, reverse sweep");
     s = grad_fused_launch(g, a, G, holders, st);
     if (s != BOAC_OK) return s;
-    phase.next("gradient (fused): mu samples -> pixels -> coefficients");
-    mbar_scan_kernel<<<ray_grid(g, B), kRayThreads, 0, st>>>(n, V, dx, P(lay.abar));
-    backproject_table(g, B, P(lay.abar), nullptr, 1.0f, P(lay.mubar), 0, P(lay.partial), st);
+    phase.next("gradient (fused): pixels -> coefficients");
     if (t)
         grad_coef_kernel<6><<<B, 256, 0, st>>>(n, (double)dx, (double)t->mu_b, (double)t->mu_c, (double)t->dR, c,
                                                P(lay.mubar), dL_dc);

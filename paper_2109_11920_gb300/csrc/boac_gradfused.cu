@@ -22,11 +22,14 @@
 //        rbar = A zbar,  qbar' = -rbar S / (q^n)^2 (0 where q^n = 0),
 //        abar += dx (r^n (B zbar) + qbar' (B F^n)),
 //        Fbar <- Fbar z^n / sens + A^T qbar';
-//   5. the sensitivity's share, abar += dx (B sensbar).
-// abar is accumulated already multiplied by the factor it belongs to (a
-// plain scan along each ray then gives the adjoint of the mu samples); the
-// scan, the transposed sampling to the pixels and the float64 reduction to
-// d/dc run as small batched kernels after this one (boac_grad.cu).
+//   5. the sensitivity's share, abar += dx (B sensbar);
+//   6. mubar, the adjoint of the pixels of mu: the transposed sampling of
+//      the mu samples' adjoint of every grid.
+// No abar is stored: each step turns its abar into the adjoint of the mu
+// samples on chip (a scan along each ray, the four views of a grid summed)
+// and adds that, one value per sample of each grid, into a per-candidate
+// buffer.  The float64 reduction of mubar to d/dc runs as a small batched
+// kernel after this one (boac_grad.cu).
 //
 // In cluster mode (G > 1) rank r walks the grids [r V'/G, (r+1) V'/G) of the
 // V' = V/4 sample grids with its own copies of the sampled images; every
@@ -50,9 +53,9 @@ namespace cg = cooperative_groups;
 namespace boac {
 
 // x += v at L2 without waiting for the old value (red.global.add).  Every
-// element of abar is updated by one thread per pass, and one thread's
-// updates of an address are applied in program order, so the sums are those
-// of a read-modify-write, bit for bit.
+// element of the mu-sample adjoint is updated by one thread per pass, and
+// one thread's updates of an address are applied in program order, so the
+// sums are those of a read-modify-write, bit for bit.
 __device__ __forceinline__ void red_add(float* p, float v) {
     asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
 }
@@ -210,53 +213,88 @@ __global__ void __launch_bounds__(8 * N, 1) grad_fused_kernel(GradFusedArgs a) {
         }
         __syncthreads();
     };
-    // abar_v(sample) += a_v dx (k1_v x + k2_v y): x the samples in W, y the
-    // samples stored by an earlier project_grid of another image (Yc: by
-    // sample (k, b) at k n + b, Yr: at b n + k; nullptr: none), k1 / k2 per
-    // ray in grid coordinates (k2 unused without y); view-ray layout of
-    // abar: view phi sample (k, b) at (k, b), phi + pi at (n-1-k, n-1-b),
-    // phi + pi/2 at (n-1-b, k), phi + 3pi/2 at (b, n-1-k).  Reads W only;
-    // the additions are fire-and-forget reductions at L2.
-    auto abar_grid = [&](int gi, float* ab, const float* k1, const float* k2, const float* Yc, const float* Yr) {
+    // The adjoint of the mu samples of grid gi, added into Mg ([k][b], grid
+    // coordinates) for one step.  Per view v the adjoint of the factor at
+    // sample s is abar_v(s) = a_v(s) dx (k1_v x(s) + k2_v y(s)), x the
+    // samples in W, y those stored by an earlier project_grid of another
+    // image (Yc: sample (k, b) at k n + b, Yr: at b n + k; nullptr: none),
+    // k1 / k2 per ray in grid coordinates.  A factor's exponent sums the mu
+    // samples between its sample and the detector (half its own), so the
+    // sample's adjoint is -dx (abar/2 + the abar of the samples farther from
+    // the detector): a prefix along k for view phi, a suffix for phi + pi, a
+    // suffix along b for phi + pi/2 and a prefix for phi + 3pi/2.  The four
+    // views of a grid share its samples, so one sum per sample is added.
+    // Each thread scans its SEG samples of a ray; the other segments enter
+    // as a constant per (ray, segment) from the segment totals.  The column
+    // views' part within the segment goes out at once; the row pass leaves
+    // its part in W, and the rest (row part and both constants) goes out as
+    // a second reduction per sample, lanes along b in both.
+    auto mubar_grid = [&](int gi, float* Mg, const float* k1, const float* k2, const float* Yc, const float* Yr) {
         const bool Y = Yc != nullptr;
         const float* Xc = tab + (gi - g0) * gstride;
         const float* XrT = Xc + NN;
         const float* Uc = Xc + 2 * NN;
         const float* Ur = Uc + N;
-        {   // column views, thread on column lb
-            float* a1 = ab + (size_t)gi * NN;
-            float* a2 = ab + (size_t)(gi + V / 2) * NN;
+        {   // views phi, phi + pi: thread on column lb
             const float uc = Uc[lb];
             const float w11 = dx * k1[lb], w12 = dx * k1[N + lb];
             const float w21 = Y ? dx * k2[lb] : 0.0f, w22 = Y ? dx * k2[N + lb] : 0.0f;
+            float p1 = 0.0f, q2 = 0.0f;
 #pragma unroll 4
             for (int s = 0; s < SEG; ++s) {
                 const int k = k0 + s;
                 const float x = W[k * WP + lb];
                 const float yv = Y ? __ldcg(Yc + k * N + lb) : 0.0f;
                 const float ye = Xc[k * N + lb];
-                const size_t i1 = (size_t)k * N + lb, i2 = (size_t)(N - 1 - k) * N + (N - 1 - lb);
-                red_add(a1 + i1, ex2(ye) * fmaf(w21, yv, w11 * x));
-                red_add(a2 + i2, ex2(uc - ye) * fmaf(w22, yv, w12 * x));
+                const float a1 = ex2(ye) * fmaf(w21, yv, w11 * x);
+                const float a2 = ex2(uc - ye) * fmaf(w22, yv, w12 * x);
+                q2 += a2;
+                red_add(Mg + k * N + lb, -dx * fmaf(0.5f, a1 + a2, p1 - q2));  // + a2 of the segment
+                p1 += a1;
             }
+            redc[seg * N + lb] = p1;
+            redc[(NSEG + seg) * N + lb] = q2;
         }
-        {   // row views, thread on row lb
-            float* a3 = ab + (size_t)(gi + V / 4) * NN;
-            float* a4 = ab + (size_t)(gi + 3 * V / 4) * NN;
+        __syncthreads();
+        {   // views phi + pi/2, phi + 3pi/2: thread on row lb
             const int k = lb;
             const float ur = Ur[k];
             const float w13 = dx * k1[2 * N + k], w14 = dx * k1[3 * N + k];
             const float w23 = Y ? dx * k2[2 * N + k] : 0.0f, w24 = Y ? dx * k2[3 * N + k] : 0.0f;
+            float q3 = 0.0f, p4 = 0.0f;
 #pragma unroll 4
             for (int s = 0; s < SEG; ++s) {
                 const int b = k0 + s;
                 const float x = W[k * WP + b];
                 const float yv = Y ? __ldcg(Yr + b * N + k) : 0.0f;
                 const float ye = XrT[b * N + k];
-                const size_t i3 = (size_t)(N - 1 - b) * N + k, i4 = (size_t)b * N + (N - 1 - k);
-                red_add(a3 + i3, ex2(ye) * fmaf(w23, yv, w13 * x));
-                red_add(a4 + i4, ex2(ur - ye) * fmaf(w24, yv, w14 * x));
+                const float a3 = ex2(ye) * fmaf(w23, yv, w13 * x);
+                const float a4 = ex2(ur - ye) * fmaf(w24, yv, w14 * x);
+                q3 += a3;
+                W[k * WP + b] = fmaf(0.5f, a3 + a4, p4 - q3);  // + a3 of the segment
+                p4 += a4;
             }
+            redr[seg * N + k] = q3;
+            redr[(NSEG + seg) * N + k] = p4;
+        }
+        __syncthreads();
+        // constants of this thread's segment: column lb (a1 of the earlier
+        // segments, a2 of this and the later ones), row lb (a3 of this and
+        // the later segments, a4 of the earlier ones)
+        float cc = 0.0f, cr = 0.0f;
+#pragma unroll
+        for (int s2 = 0; s2 < NSEG; ++s2) {
+            cc += s2 < seg ? redc[s2 * N + lb] : redc[(NSEG + s2) * N + lb];
+            cr += s2 >= seg ? redr[s2 * N + lb] : redr[(NSEG + s2) * N + lb];
+        }
+        __syncthreads();
+        redr[seg * N + lb] = cr;
+        __syncthreads();
+        const float* crow = redr + (lb / SEG) * N;  // row constants of column lb's segment
+#pragma unroll
+        for (int s = 0; s < SEG; ++s) {
+            const int k = k0 + s;
+            red_add(Mg + k * N + lb, -dx * (W[k * WP + lb] + crow[k] + cc));
         }
         __syncthreads();
     };
@@ -304,7 +342,7 @@ __global__ void __launch_bounds__(8 * N, 1) grad_fused_kernel(GradFusedArgs a) {
         float* segq = a.segq + (size_t)cand * a.ckpt * V * N;
         float* Fbar = a.Fbar + (size_t)cand * NN;
         float* sensbar = a.sensbar + (size_t)cand * NN;
-        float* ab = a.abar + (size_t)cand * V * NN;
+        float* Ms = a.abar + (size_t)cand * ngrid * NN;
         float* segB = a.segB + (size_t)cand * a.ckpt * ngrid * NN;
         float* segBT = a.segBT + (size_t)cand * a.ckpt * ngrid * NN;
 
@@ -315,12 +353,9 @@ __global__ void __launch_bounds__(8 * N, 1) grad_fused_kernel(GradFusedArgs a) {
         }
         __syncthreads();
         for (int i = tid; i < NN; i += NT) img0[pad(i)] = __ldg(mu + i);
-        // abar of this rank's views starts at 0; sensbar (this rank's rows) too
-        for (int gi = g0; gi < g1; ++gi)
-            for (int vi = 0; vi < 4; ++vi) {
-                float* av = ab + (size_t)(gi + vi * (V / 4)) * NN;
-                for (int i = tid; i < NN; i += NT) av[i] = 0.0f;
-            }
+        // the mu-sample adjoint of this rank's grids starts at 0; sensbar
+        // (this rank's rows) too
+        for (size_t i = (size_t)g0 * NN + tid; i < (size_t)g1 * NN; i += NT) Ms[i] = 0.0f;
         for (int i = R0 * N + tid; i < R1 * N; i += NT) sensbar[i] = 0.0f;
         __syncthreads();
         for (int gi = g0; gi < g1; ++gi) {
@@ -444,7 +479,7 @@ __global__ void __launch_bounds__(8 * N, 1) grad_fused_kernel(GradFusedArgs a) {
                 c1[u] = s > 0.0f ? (q > 0.0f ? s / q - 1.0f : 0.0f) : -1.0f;
             }
             __syncthreads();
-            abar_grid(gi, ab, c1, nullptr, nullptr, nullptr);  // W holds B F^K
+            mubar_grid(gi, Ms + (size_t)gi * NN, c1, nullptr, nullptr, nullptr);  // W holds B F^K
             backproject_grid(gi, c1);
         }
         for (int off = 16; off > 0; off >>= 1) lacc += __shfl_down_sync(0xffffffffu, lacc, off);
@@ -511,8 +546,8 @@ __global__ void __launch_bounds__(8 * N, 1) grad_fused_kernel(GradFusedArgs a) {
                         c2[u] = q > 0.0f ? -qv[u] * (s / (q * q)) : 0.0f;      // qbar'
                     }
                     __syncthreads();
-                    abar_grid(gi, ab, c1, c2, segB + ((size_t)t * ngrid + gi) * NN,
-                              segBT + ((size_t)t * ngrid + gi) * NN);  // y = B F^n
+                    mubar_grid(gi, Ms + (size_t)gi * NN, c1, c2, segB + ((size_t)t * ngrid + gi) * NN,
+                               segBT + ((size_t)t * ngrid + gi) * NN);  // y = B F^n
                     backproject_grid(gi, c2);
                 }
                 cluster_sync();
@@ -530,9 +565,25 @@ __global__ void __launch_bounds__(8 * N, 1) grad_fused_kernel(GradFusedArgs a) {
         __syncthreads();
         for (int gi = g0; gi < g1; ++gi) {
             project_grid(gi, S, nullptr, nullptr);  // W <- B sensbar
-            abar_grid(gi, ab, c1, nullptr, nullptr, nullptr);
+            mubar_grid(gi, Ms + (size_t)gi * NN, c1, nullptr, nullptr, nullptr);
         }
+
+        // ---- 6. the mu samples' adjoint to the pixels: mubar = sum over
+        // grids of the transposed sampling of Ms (img1 is clear here)
+        for (int gi = g0; gi < g1; ++gi) {
+            const unsigned short* gs = a.sched + (size_t)gi * 9 * CE;
+            SchedSlots<N, NT> sched0;
+            sched0.load(gs);
+            const float* Mg = Ms + (size_t)gi * NN;
+#pragma unroll 4
+            for (int s = 0; s < SEG; ++s) W[(k0 + s) * WP + lb] = __ldcg(Mg + (k0 + s) * N + lb);
+            __syncthreads();
+            scatter_scheduled<N, NT, P, WP>(W, img1, csn[2 * gi], csn[2 * gi + 1], c, gs, sched0);
+        }
+        cluster_sync();
+        for (int i = R0 * N + tid; i < R1 * N; i += NT) a.mubar[(size_t)cand * NN + i] = acc_sum(pad(i));
         cluster_sync();  // no rank still reads another's memory
+        clear_acc();
     }
 }
 
