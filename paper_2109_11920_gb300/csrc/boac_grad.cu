@@ -357,7 +357,7 @@ static GradLayout grad_layout(const boac_geom* g, int B, int K, int ckpt) {
 // mubar; the grouped back-projection's partials;
 // the ln S! scratch and the scatter schedule.
 struct GradFusedLayout {
-    size_t mu, tab, sens, ck, segF, segz, segq, segB, segBT, Fbar, sensbar, abar, mubar, lg, sched, total;
+    size_t mu, tab, sens, ck, segF, segz, segq, segB, Fbar, sensbar, abar, mubar, lg, sched, total;
 };
 
 static GradFusedLayout grad_fused_layout(const boac_geom* g, int B, int K, int ckpt, int G, int holders) {
@@ -379,7 +379,6 @@ static GradFusedLayout grad_fused_layout(const boac_geom* g, int B, int K, int c
     L.segz = take(Bs * (size_t)ckpt * nn);
     L.segq = take(Bs * (size_t)ckpt * vb);
     L.segB = take(Bs * (size_t)ckpt * (g->n_views / 4) * nn);
-    L.segBT = take(Bs * (size_t)ckpt * (g->n_views / 4) * nn);
     L.Fbar = take(Bs * nn);
     L.sensbar = take(Bs * nn);
     L.abar = take(Bs * (size_t)(g->n_views / 4) * nn);
@@ -427,7 +426,6 @@ static int score_grad_fused_run(const boac_geom* g, const boac_tissue* t, const 
     a.segz = P(lay.segz);
     a.segq = P(lay.segq);
     a.segB = P(lay.segB);
-    a.segBT = P(lay.segBT);
     a.Fbar = P(lay.Fbar);
     a.sensbar = P(lay.sensbar);
     a.abar = P(lay.abar);

@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(8 * N, 1) grad_fused_kernel(GradFusedArgs a) {
     // sample for views phi, phi + pi (columns) and phi +- pi/2 (rows), in grid
     // coordinates.  Also stages the grid's sinogram rows into Sg (by grid
     // coordinate: S of view phi + pi and phi + 3pi/2 reversed).
-    auto project_grid = [&](int gi, const float* S, float* bf, float* bft) {
+    auto project_grid = [&](int gi, const float* S, float* bf) {
         const float cs = csn[2 * gi], sn = csn[2 * gi + 1];
         const float* Xc = tab + (gi - g0) * gstride;
         const float* XrT = Xc + NN;
@@ -194,7 +194,6 @@ __global__ void __launch_bounds__(8 * N, 1) grad_fused_kernel(GradFusedArgs a) {
             for (int s = 0; s < SEG; ++s) {
                 const int b = k0 + s;
                 const float f = W[lb * WP + b];
-                if (bft) bft[b * N + lb] = f;
                 const float y = XrT[b * N + lb];
                 acc3 = fmaf(ex2(y), f, acc3);
                 acc4 = fmaf(ex2(ur - y), f, acc4);
@@ -217,7 +216,7 @@ __global__ void __launch_bounds__(8 * N, 1) grad_fused_kernel(GradFusedArgs a) {
     // coordinates) for one step.  Per view v the adjoint of the factor at
     // sample s is abar_v(s) = a_v(s) dx (k1_v x(s) + k2_v y(s)), x the
     // samples in W, y those stored by an earlier project_grid of another
-    // image (Yc: sample (k, b) at k n + b, Yr: at b n + k; nullptr: none),
+    // image (sample (k, b) at Yc[k n + b]; nullptr: none),
     // k1 / k2 per ray in grid coordinates.  A factor's exponent sums the mu
     // samples between its sample and the detector (half its own), so the
     // sample's adjoint is -dx (abar/2 + the abar of the samples farther from
@@ -229,7 +228,7 @@ __global__ void __launch_bounds__(8 * N, 1) grad_fused_kernel(GradFusedArgs a) {
     // views' part within the segment goes out at once; the row pass leaves
     // its part in W, and the rest (row part and both constants) goes out as
     // a second reduction per sample, lanes along b in both.
-    auto mubar_grid = [&](int gi, float* Mg, const float* k1, const float* k2, const float* Yc, const float* Yr) {
+    auto mubar_grid = [&](int gi, float* Mg, const float* k1, const float* k2, const float* Yc) {
         const bool Y = Yc != nullptr;
         const float* Xc = tab + (gi - g0) * gstride;
         const float* XrT = Xc + NN;
@@ -262,17 +261,24 @@ __global__ void __launch_bounds__(8 * N, 1) grad_fused_kernel(GradFusedArgs a) {
             const float w13 = dx * k1[2 * N + k], w14 = dx * k1[3 * N + k];
             const float w23 = Y ? dx * k2[2 * N + k] : 0.0f, w24 = Y ? dx * k2[3 * N + k] : 0.0f;
             float q3 = 0.0f, p4 = 0.0f;
-#pragma unroll 4
-            for (int s = 0; s < SEG; ++s) {
-                const int b = k0 + s;
-                const float x = W[k * WP + b];
-                const float yv = Y ? __ldcg(Yr + b * N + k) : 0.0f;
-                const float ye = XrT[b * N + k];
-                const float a3 = ex2(ye) * fmaf(w23, yv, w13 * x);
-                const float a4 = ex2(ur - ye) * fmaf(w24, yv, w14 * x);
-                q3 += a3;
-                W[k * WP + b] = fmaf(0.5f, a3 + a4, p4 - q3);  // + a3 of the segment
-                p4 += a4;
+            // y of the row's SEG samples, four at a time (16-byte aligned:
+            // n and k0 are multiples of 4)
+#pragma unroll 1
+            for (int s4 = 0; s4 < SEG; s4 += 4) {
+                const float4 y4 = Y ? __ldcg(reinterpret_cast<const float4*>(Yc + k * N + k0 + s4))
+                                    : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                const float yy[4] = {y4.x, y4.y, y4.z, y4.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int b = k0 + s4 + j;
+                    const float x = W[k * WP + b];
+                    const float ye = XrT[b * N + k];
+                    const float a3 = ex2(ye) * fmaf(w23, yy[j], w13 * x);
+                    const float a4 = ex2(ur - ye) * fmaf(w24, yy[j], w14 * x);
+                    q3 += a3;
+                    W[k * WP + b] = fmaf(0.5f, a3 + a4, p4 - q3);  // + a3 of the segment
+                    p4 += a4;
+                }
             }
             redr[seg * N + k] = q3;
             redr[(NSEG + seg) * N + k] = p4;
@@ -344,7 +350,6 @@ __global__ void __launch_bounds__(8 * N, 1) grad_fused_kernel(GradFusedArgs a) {
         float* sensbar = a.sensbar + (size_t)cand * NN;
         float* Ms = a.abar + (size_t)cand * ngrid * NN;
         float* segB = a.segB + (size_t)cand * a.ckpt * ngrid * NN;
-        float* segBT = a.segBT + (size_t)cand * a.ckpt * ngrid * NN;
 
         // ---- 1. set-up: mu -> img0, exponents of this rank's grids, sens
         for (int i = tid; i < IMG; i += NT) {
@@ -437,8 +442,7 @@ __global__ void __launch_bounds__(8 * N, 1) grad_fused_kernel(GradFusedArgs a) {
                 for (int i = R0 * N + tid; i < R1 * N; i += NT) segF[(size_t)t * NN + i] = img0[pad(i)];
             for (int gi = g0; gi < g1; ++gi) {
                 // (rec: the samples of F^n too, for the reverse step's abar)
-                project_grid(gi, S, rec ? segB + ((size_t)t * ngrid + gi) * NN : nullptr,
-                             rec ? segBT + ((size_t)t * ngrid + gi) * NN : nullptr);
+                project_grid(gi, S, rec ? segB + ((size_t)t * ngrid + gi) * NN : nullptr);
                 for (int u = tid; u < 4 * N; u += NT) {
                     const float q = qv[u];
                     if (rec) segq[((size_t)t * ngrid + gi) * 4 * N + u] = q;
@@ -472,14 +476,14 @@ __global__ void __launch_bounds__(8 * N, 1) grad_fused_kernel(GradFusedArgs a) {
         // ---- 3. score at F^K and its adjoint
         double lacc = 0.0;
         for (int gi = g0; gi < g1; ++gi) {
-            project_grid(gi, S, nullptr, nullptr);
+            project_grid(gi, S, nullptr);
             for (int u = tid; u < 4 * N; u += NT) {
                 const float s = Sg[u], q = qv[u];
                 lacc += loglik_term(s, q, a.include_lgamma && !a.lgS);
                 c1[u] = s > 0.0f ? (q > 0.0f ? s / q - 1.0f : 0.0f) : -1.0f;
             }
             __syncthreads();
-            mubar_grid(gi, Ms + (size_t)gi * NN, c1, nullptr, nullptr, nullptr);  // W holds B F^K
+            mubar_grid(gi, Ms + (size_t)gi * NN, c1, nullptr, nullptr);  // W holds B F^K
             backproject_grid(gi, c1);
         }
         for (int off = 16; off > 0; off >>= 1) lacc += __shfl_down_sync(0xffffffffu, lacc, off);
@@ -539,15 +543,14 @@ __global__ void __launch_bounds__(8 * N, 1) grad_fused_kernel(GradFusedArgs a) {
                 }
                 cluster_sync();
                 for (int gi = g0; gi < g1; ++gi) {
-                    project_grid(gi, S, nullptr, nullptr);  // W <- B zbar, qv <- A zbar (rbar)
+                    project_grid(gi, S, nullptr);  // W <- B zbar, qv <- A zbar (rbar)
                     for (int u = tid; u < 4 * N; u += NT) {
                         const float q = __ldcg(segq + ((size_t)t * ngrid + gi) * 4 * N + u), s = Sg[u];
                         c1[u] = q > 0.0f ? s / q : 0.0f;                       // r^n
                         c2[u] = q > 0.0f ? -qv[u] * (s / (q * q)) : 0.0f;      // qbar'
                     }
                     __syncthreads();
-                    mubar_grid(gi, Ms + (size_t)gi * NN, c1, c2, segB + ((size_t)t * ngrid + gi) * NN,
-                               segBT + ((size_t)t * ngrid + gi) * NN);  // y = B F^n
+                    mubar_grid(gi, Ms + (size_t)gi * NN, c1, c2, segB + ((size_t)t * ngrid + gi) * NN);  // y = B F^n
                     backproject_grid(gi, c2);
                 }
                 cluster_sync();
@@ -564,8 +567,8 @@ __global__ void __launch_bounds__(8 * N, 1) grad_fused_kernel(GradFusedArgs a) {
         for (int t = tid; t < 4 * N; t += NT) c1[t] = 1.0f;
         __syncthreads();
         for (int gi = g0; gi < g1; ++gi) {
-            project_grid(gi, S, nullptr, nullptr);  // W <- B sensbar
-            mubar_grid(gi, Ms + (size_t)gi * NN, c1, nullptr, nullptr, nullptr);
+            project_grid(gi, S, nullptr);  // W <- B sensbar
+            mubar_grid(gi, Ms + (size_t)gi * NN, c1, nullptr, nullptr);
         }
 
         // ---- 6. the mu samples' adjoint to the pixels: mubar = sum over
