@@ -121,7 +121,7 @@ struct GradFusedArgs {
     float* segF;        // per candidate: [ckpt + 1][n^2] iterates of a segment
     float* segz;        // per candidate: [ckpt][n^2] z^n = A^T r^n
     float* segq;        // per candidate: [ckpt][V / 4][4][n] q^n in grid coordinates
-    float* segB;        // per candidate: [ckpt][V / 4][n][n] samples (k, b) of F^n per grid
+    float* segB;        // per candidate: [ckpt][V / 4][n][n] sample (k, b) of F^n at [b][k]
     float* Fbar;        // per candidate: [n^2]
     float* sensbar;     // per candidate: [n^2]
     float* abar;        // per candidate: [V / 4][n][n] adjoint of the mu samples of each grid

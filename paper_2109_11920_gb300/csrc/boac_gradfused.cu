@@ -52,13 +52,11 @@ namespace cg = cooperative_groups;
 
 namespace boac {
 
-// x += v at L2 without waiting for the old value (red.global.add).  Every
-// element of the mu-sample adjoint is updated by one thread per pass, and
-// one thread's updates of an address are applied in program order, so the
-// sums are those of a read-modify-write, bit for bit.
-__device__ __forceinline__ void red_add(float* p, float v) {
-    asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
-}
+// x += v at L2, the old value not returned (a reduction, not a load and a
+// store).  Every element of the mu-sample adjoint is updated by one thread
+// per pass, and one thread's updates of an address are applied in program
+// order, so the sums are those of a read-modify-write, bit for bit.
+__device__ __forceinline__ void red_add(float* p, float v) { atomicAdd(p, v); }
 
 template <int N>
 struct GradShape {
@@ -171,6 +169,7 @@ __global__ void __launch_bounds__(8 * N, 1) grad_fused_kernel(GradFusedArgs a) {
         {
             const float uc = Uc[lb];
             float acc1 = 0.0f, acc2 = 0.0f;
+            float fq[4];
 #pragma unroll 8
             for (int s = 0; s < SEG; ++s) {
                 const int k = k0 + s;
@@ -178,7 +177,9 @@ __global__ void __launch_bounds__(8 * N, 1) grad_fused_kernel(GradFusedArgs a) {
                 sample_uw(k, lb, cs, sn, c, &u, &w);
                 const float f = bilerp_padded(img0, P, N, u, w);
                 W[k * WP + lb] = f;
-                if (bf) bf[k * N + lb] = f;
+                fq[s & 3] = f;  // bf: sample (k, b) at b n + k, four k per store, read once
+                if ((s & 3) == 3 && bf)
+                    __stcs(reinterpret_cast<float4*>(bf + lb * N + k - 3), make_float4(fq[0], fq[1], fq[2], fq[3]));
                 const float y = Xc[k * N + lb];
                 acc1 = fmaf(ex2(y), f, acc1);
                 acc2 = fmaf(ex2(uc - y), f, acc2);
@@ -216,7 +217,7 @@ __global__ void __launch_bounds__(8 * N, 1) grad_fused_kernel(GradFusedArgs a) {
     // coordinates) for one step.  Per view v the adjoint of the factor at
     // sample s is abar_v(s) = a_v(s) dx (k1_v x(s) + k2_v y(s)), x the
     // samples in W, y those stored by an earlier project_grid of another
-    // image (sample (k, b) at Yc[k n + b]; nullptr: none),
+    // image (sample (k, b) at Yc[b n + k]; nullptr: none),
     // k1 / k2 per ray in grid coordinates.  A factor's exponent sums the mu
     // samples between its sample and the detector (half its own), so the
     // sample's adjoint is -dx (abar/2 + the abar of the samples farther from
@@ -239,17 +240,22 @@ __global__ void __launch_bounds__(8 * N, 1) grad_fused_kernel(GradFusedArgs a) {
             const float w11 = dx * k1[lb], w12 = dx * k1[N + lb];
             const float w21 = Y ? dx * k2[lb] : 0.0f, w22 = Y ? dx * k2[N + lb] : 0.0f;
             float p1 = 0.0f, q2 = 0.0f;
-#pragma unroll 4
-            for (int s = 0; s < SEG; ++s) {
-                const int k = k0 + s;
-                const float x = W[k * WP + lb];
-                const float yv = Y ? __ldcg(Yc + k * N + lb) : 0.0f;
-                const float ye = Xc[k * N + lb];
-                const float a1 = ex2(ye) * fmaf(w21, yv, w11 * x);
-                const float a2 = ex2(uc - ye) * fmaf(w22, yv, w12 * x);
-                q2 += a2;
-                red_add(Mg + k * N + lb, -dx * fmaf(0.5f, a1 + a2, p1 - q2));  // + a2 of the segment
-                p1 += a1;
+#pragma unroll 1
+            for (int s4 = 0; s4 < SEG; s4 += 4) {
+                const float4 y4 = Y ? __ldcg(reinterpret_cast<const float4*>(Yc + lb * N + k0 + s4))
+                                    : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                const float yy[4] = {y4.x, y4.y, y4.z, y4.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int k = k0 + s4 + j;
+                    const float x = W[k * WP + lb];
+                    const float ye = Xc[k * N + lb];
+                    const float a1 = ex2(ye) * fmaf(w21, yy[j], w11 * x);
+                    const float a2 = ex2(uc - ye) * fmaf(w22, yy[j], w12 * x);
+                    q2 += a2;
+                    red_add(Mg + k * N + lb, -dx * fmaf(0.5f, a1 + a2, p1 - q2));  // + a2 of the segment
+                    p1 += a1;
+                }
             }
             redc[seg * N + lb] = p1;
             redc[(NSEG + seg) * N + lb] = q2;
@@ -261,24 +267,17 @@ __global__ void __launch_bounds__(8 * N, 1) grad_fused_kernel(GradFusedArgs a) {
             const float w13 = dx * k1[2 * N + k], w14 = dx * k1[3 * N + k];
             const float w23 = Y ? dx * k2[2 * N + k] : 0.0f, w24 = Y ? dx * k2[3 * N + k] : 0.0f;
             float q3 = 0.0f, p4 = 0.0f;
-            // y of the row's SEG samples, four at a time (16-byte aligned:
-            // n and k0 are multiples of 4)
-#pragma unroll 1
-            for (int s4 = 0; s4 < SEG; s4 += 4) {
-                const float4 y4 = Y ? __ldcg(reinterpret_cast<const float4*>(Yc + k * N + k0 + s4))
-                                    : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-                const float yy[4] = {y4.x, y4.y, y4.z, y4.w};
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int b = k0 + s4 + j;
-                    const float x = W[k * WP + b];
-                    const float ye = XrT[b * N + k];
-                    const float a3 = ex2(ye) * fmaf(w23, yy[j], w13 * x);
-                    const float a4 = ex2(ur - ye) * fmaf(w24, yy[j], w14 * x);
-                    q3 += a3;
-                    W[k * WP + b] = fmaf(0.5f, a3 + a4, p4 - q3);  // + a3 of the segment
-                    p4 += a4;
-                }
+#pragma unroll 4
+            for (int s = 0; s < SEG; ++s) {
+                const int b = k0 + s;
+                const float x = W[k * WP + b];
+                const float yv = Y ? __ldcg(Yc + b * N + k) : 0.0f;
+                const float ye = XrT[b * N + k];
+                const float a3 = ex2(ye) * fmaf(w23, yv, w13 * x);
+                const float a4 = ex2(ur - ye) * fmaf(w24, yv, w14 * x);
+                q3 += a3;
+                W[k * WP + b] = fmaf(0.5f, a3 + a4, p4 - q3);  // + a3 of the segment
+                p4 += a4;
             }
             redr[seg * N + k] = q3;
             redr[(NSEG + seg) * N + k] = p4;
