@@ -241,13 +241,19 @@ __global__ void mlem_step_adjoint_kernel(long long count, const float* __restric
 // and with NP = 9 (per-candidate tissue values after the coefficients) also
 //   dL/dmu_b = sum mubar f(R),  dL/dmu_c = sum mubar (f(R + dR) - f(R)),
 //   dL/ddR = sum mubar mu_c f'(R + dR) [dR > 0],
-// accumulated in float64 with a fixed reduction tree.  One block per candidate.
+// accumulated in float64 with a fixed reduction tree: block (cand, h) sums
+// the pixels of part h of kCoefParts (a fixed split, so a candidate's
+// gradient does not depend on the batch) into part_out[cand][h][NP], and
+// grad_coef_sum_kernel adds the parts in order.
+constexpr int kCoefParts = 8;
 template <int NP>
 __global__ void grad_coef_kernel(int n, double dx, double mu_b0, double mu_c0, double dR0,
                                  const float* __restrict__ coef, const float* __restrict__ mubar,
-                                 double* __restrict__ grad) {
+                                 double* __restrict__ part_out) {
     __shared__ double part[32][NP];
-    const int cand = blockIdx.x;
+    const int cand = blockIdx.x, h = blockIdx.y;
+    const int chunk = (n * n + kCoefParts - 1) / kCoefParts;
+    const int p0 = h * chunk, p1 = p0 + chunk < n * n ? p0 + chunk : n * n;
     double c6[6];
 #pragma unroll
     for (int k = 0; k < 6; ++k) c6[k] = (double)__ldg(coef + cand * NP + k);
@@ -263,7 +269,7 @@ __global__ void grad_coef_kernel(int n, double dx, double mu_b0, double mu_c0, d
     for (int k = 0; k < NP; ++k) acc[k] = 0.0;
     const double cc = 0.5 * (double)(n - 1);
     const float* mb = mubar + (size_t)cand * n * n;
-    for (int pix = threadIdx.x; pix < n * n; pix += blockDim.x) {
+    for (int pix = p0 + threadIdx.x; pix < p1; pix += blockDim.x) {
         const int i = pix / n, j = pix % n;
         const double x = ((double)j - cc) * dx, y = ((double)i - cc) * dx;
         const double r = sqrt(x * x + y * y);
@@ -305,14 +311,41 @@ __global__ void grad_coef_kernel(int n, double dx, double mu_b0, double mu_c0, d
     if (threadIdx.x < NP) {
         double t = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w][threadIdx.x];
-        grad[cand * NP + threadIdx.x] = t;
+        part_out[((size_t)cand * kCoefParts + h) * NP + threadIdx.x] = t;
+    }
+}
+
+template <int NP>
+__global__ void grad_coef_sum_kernel(int B, const double* __restrict__ part, double* __restrict__ grad) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= B * NP) return;
+    const int cand = i / NP, k = i % NP;
+    double t = 0.0;
+    for (int h = 0; h < kCoefParts; ++h) t += part[((size_t)cand * kCoefParts + h) * NP + k];
+    grad[i] = t;
+}
+
+// mubar -> dL/dc (t != nullptr: c[B][6] with t's tissue values) or dL/dp
+// (t == nullptr: p[B][9]); part: B * kCoefParts * kParams doubles.
+static void coef_launch(const boac_geom* g, const boac_tissue* t, const float* c, const float* mubar, int B,
+                        double* part, double* dL_dc, cudaStream_t st) {
+    const int n = g->n;
+    const double dx = (double)g->pixel_cm;
+    const dim3 grid((unsigned)B, kCoefParts);
+    if (t) {
+        grad_coef_kernel<6><<<grid, 256, 0, st>>>(n, dx, (double)t->mu_b, (double)t->mu_c, (double)t->dR, c, mubar,
+                                                  part);
+        grad_coef_sum_kernel<6><<<(B * 6 + 255) / 256, 256, 0, st>>>(B, part, dL_dc);
+    } else {
+        grad_coef_kernel<kParams><<<grid, 256, 0, st>>>(n, dx, 0.0, 0.0, 0.0, c, mubar, part);
+        grad_coef_sum_kernel<kParams><<<(B * kParams + 255) / 256, 256, 0, st>>>(B, part, dL_dc);
     }
 }
 
 // ------------------------------------------------------------- workspace
 struct GradLayout {
     size_t mu, tab, abar, sens, sensbar, Fbar, Fnew, zbar, mubar, Fk, ck, Fseg, zseg, qseg, rseg, qK,
-        qbar, rbar, partial, lg, total;
+        qbar, rbar, partial, lg, coefp, total;
 };
 
 static GradLayout grad_layout(const boac_geom* g, int B, int K, int ckpt) {
@@ -346,6 +379,7 @@ static GradLayout grad_layout(const boac_geom* g, int B, int K, int ckpt) {
     L.rbar = take(Bs * vb);
     L.partial = take(bp_partial_floats(g, B));
     L.lg = take(2 * kLgammaScratchDoubles);  // the ln S! sum of a shared sinogram
+    L.coefp = take(2 * Bs * kCoefParts * kParams);  // doubles
     L.total = off;
     return L;
 }
@@ -353,11 +387,11 @@ static GradLayout grad_layout(const boac_geom* g, int B, int K, int ckpt) {
 // Workspace of the fused gradient (boac_gradfused.cu) with cluster size G on
 // `holders` clusters: per CTA its exponent slot and sensitivity rows; per
 // candidate the AREA map, checkpoints, segment iterates (with their samples
-// on every grid, two layouts), Fbar, sensbar, the attenuation adjoint and
-// mubar; the grouped back-projection's partials;
-// the ln S! scratch and the scatter schedule.
+// on every grid), Fbar, sensbar, the adjoint of the mu samples of every grid
+// and mubar; the ln S! scratch, the coefficient reduction's partial sums and
+// the scatter schedule.
 struct GradFusedLayout {
-    size_t mu, tab, sens, ck, segF, segz, segq, segB, Fbar, sensbar, abar, mubar, lg, sched, total;
+    size_t mu, tab, sens, ck, segF, segz, segq, segB, Fbar, sensbar, abar, mubar, lg, coefp, sched, total;
 };
 
 static GradFusedLayout grad_fused_layout(const boac_geom* g, int B, int K, int ckpt, int G, int holders) {
@@ -384,6 +418,7 @@ static GradFusedLayout grad_fused_layout(const boac_geom* g, int B, int K, int c
     L.abar = take(Bs * (size_t)(g->n_views / 4) * nn);
     L.mubar = take(Bs * nn);
     L.lg = take(2 * kLgammaScratchDoubles);
+    L.coefp = take(2 * Bs * kCoefParts * kParams);  // doubles
     L.sched = off;
     off += sched_bytes(g->n, g->n_views / 4);
     L.total = off;
@@ -400,7 +435,7 @@ static int score_grad_fused_run(const boac_geom* g, const boac_tissue* t, const 
     if (!ws || ws_bytes < lay.total) return BOAC_EWORKSPACE;
     char* base = static_cast<char*>(ws);
     auto P = [&](size_t off) { return reinterpret_cast<float*>(base + off); };
-    const int n = g->n, V = g->n_views;
+    const int V = g->n_views;
     const float dx = g->pixel_cm;
     const size_t vb = (size_t)V * g->n_bins;
     NvtxPhases phase("gradient (fused): rasterise");
@@ -437,11 +472,7 @@ static int score_grad_fused_run(const boac_geom* g, const boac_tissue* t, const 
     s = grad_fused_launch(g, a, G, holders, st);
     if (s != BOAC_OK) return s;
     phase.next("gradient (fused): pixels -> coefficients");
-    if (t)
-        grad_coef_kernel<6><<<B, 256, 0, st>>>(n, (double)dx, (double)t->mu_b, (double)t->mu_c, (double)t->dR, c,
-                                               P(lay.mubar), dL_dc);
-    else
-        grad_coef_kernel<kParams><<<B, 256, 0, st>>>(n, (double)dx, 0.0, 0.0, 0.0, c, P(lay.mubar), dL_dc);
+    coef_launch(g, t, c, P(lay.mubar), B, reinterpret_cast<double*>(base + lay.coefp), dL_dc, st);
     return launch_status();
 }
 
@@ -575,11 +606,7 @@ static int score_grad_run(const boac_geom* g, const boac_tissue* t, const float*
     // attenuation -> mu samples -> pixels -> coefficients
     mbar_kernel<<<rg, kRayThreads, 0, st>>>(n, V, dx, tab, abar);
     backproject_table(g, B, abar, nullptr, 1.0f, mubar, 0, partial, st);
-    if (t)
-        grad_coef_kernel<6><<<B, 256, 0, st>>>(n, (double)dx, (double)t->mu_b, (double)t->mu_c,
-                                               (double)t->dR, c, mubar, dL_dc);
-    else
-        grad_coef_kernel<kParams><<<B, 256, 0, st>>>(n, (double)dx, 0.0, 0.0, 0.0, c, mubar, dL_dc);
+    coef_launch(g, t, c, mubar, B, reinterpret_cast<double*>(base + lay.coefp), dL_dc, st);
     return launch_status();
 }
 
