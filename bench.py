@@ -482,8 +482,9 @@ def run_gpu(args, rank, world, local_rank):
         "memory_traffic": mem,
         "e2e": e2e,
         # per step: rasterize_kernel, lgamma_partial_kernel, lgamma_final_kernel,
-        # scatter_schedule_kernel and mlem_fused_kernel
-        "gpu_launches": 5 * args.steps,
+        # scatter_schedule_kernel (returns at once once the schedule is cached),
+        # sched_tag_kernel and mlem_fused_kernel
+        "gpu_launches": 6 * args.steps,
         "clocks": clk.summary(),
     }
     if plain is not None:

@@ -628,13 +628,14 @@ template <int N, int NT, int G>
 static int split_launch_t(const FusedArgs& a, int clusters, cudaStream_t st) {
     int s = split_attrs<N, NT, G>();
     if (s != BOAC_OK) return s;
-    if (a.sched) {  // the scatter schedule of this geometry, then the kernel
-        s = sched_launch(N, a.V, a.V / 4, const_cast<unsigned short*>(a.sched), st);
+    FusedArgs b = a;
+    if (b.sched) {  // the scatter schedule of this geometry, then the kernel
+        b.sched = sched_prepare(N, b.V, b.V / 4, const_cast<unsigned short*>(a.sched), st, &s);
         if (s != BOAC_OK) return s;
     }
     cudaLaunchAttribute attr[1];
-    cudaLaunchConfig_t cfg = split_config<N, NT, G>(clusters, a.V, st, attr);
-    if (cudaLaunchKernelEx(&cfg, mlem_fused_kernel<N, NT, true, G>, a) != cudaSuccess) return launch_status();
+    cudaLaunchConfig_t cfg = split_config<N, NT, G>(clusters, b.V, st, attr);
+    if (cudaLaunchKernelEx(&cfg, mlem_fused_kernel<N, NT, true, G>, b) != cudaSuccess) return launch_status();
     return launch_status();
 }
 
@@ -651,13 +652,15 @@ static int fused_launch_t(const FusedArgs& a, int slots, cudaStream_t st) {
             return launch_status();
         attr_set[dev] = true;
     }
+    FusedArgs b = a;
     if constexpr (N <= 128) {
-        if (a.sched) {  // the scatter schedule of this geometry, then the kernel
-            const int s = sched_launch(N, a.V, QUAD ? a.V / 4 : a.V / 2, const_cast<unsigned short*>(a.sched), st);
+        if (b.sched) {  // the scatter schedule of this geometry, then the kernel
+            int s = BOAC_OK;
+            b.sched = sched_prepare(N, b.V, QUAD ? b.V / 4 : b.V / 2, const_cast<unsigned short*>(a.sched), st, &s);
             if (s != BOAC_OK) return s;
         }
     }
-    mlem_fused_kernel<N, NT, QUAD><<<slots, NT, fused_smem_bytes<N, NT>(a.V), st>>>(a);
+    mlem_fused_kernel<N, NT, QUAD><<<slots, NT, fused_smem_bytes<N, NT>(b.V), st>>>(b);
     return launch_status();
 }
 

@@ -137,7 +137,8 @@ bool grad_fused_supported(const boac_geom* g);
 int grad_fused_plan(const boac_geom* g, int B, int* holders);
 // Floats of one CTA's exponent slot for cluster size G.
 size_t grad_fused_tab_floats(const boac_geom* g, int G);
-// The scatter schedule of the geometry (into a.sched), then the kernel.
+// The scatter schedule of the geometry (cached on the device, else built
+// into a.sched), then the kernel.
 int grad_fused_launch(const boac_geom* g, const GradFusedArgs& a, int G, int clusters, cudaStream_t st);
 
 // ---- cluster kernel (boac_band.cu): images of side n split into bands of

@@ -723,9 +723,11 @@ static int grad_launch_t(const GradFusedArgs& a, int clusters, cudaStream_t st) 
     return launch_status();
 }
 
-int grad_fused_launch(const boac_geom* g, const GradFusedArgs& a, int G, int clusters, cudaStream_t st) {
+int grad_fused_launch(const boac_geom* g, const GradFusedArgs& args, int G, int clusters, cudaStream_t st) {
     if (clusters < 1) return BOAC_EINVAL;
-    int s = sched_launch(g->n, g->n_views, g->n_views / 4, const_cast<unsigned short*>(a.sched), st);
+    GradFusedArgs a = args;
+    int s = BOAC_OK;
+    a.sched = sched_prepare(g->n, g->n_views, g->n_views / 4, const_cast<unsigned short*>(args.sched), st, &s);
     if (s != BOAC_OK) return s;
 #define X(NV)                                                           \
     if (g->n == NV) {                                                   \

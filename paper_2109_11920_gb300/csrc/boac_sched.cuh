@@ -1,6 +1,7 @@
 // boac_sched.cuh -- the bank-balanced scatter schedule of the fused
-// kernels' race-free class scatter (built per call by a small kernel from
-// the geometry alone) and the scheduled scatter itself.
+// kernels' race-free class scatter (built by a small kernel from the
+// geometry alone, and kept on the device across calls by
+// boac_schedcache.cu) and the scheduled scatter itself.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -51,9 +52,20 @@ inline size_t sched_bytes(int n, int ngrid) {
     return align256(sizeof(unsigned short) * 9 * sched_entries(n) * (size_t)ngrid);
 }
 
+// Tag of a cached schedule: the geometry it was built for (never 0).
+__host__ __device__ constexpr unsigned long long sched_tag_value(int n, int V, int ngrid) {
+    return 0xB0AC5C0000000000ull ^ ((unsigned long long)n << 40) ^ ((unsigned long long)V << 20) ^
+           (unsigned long long)ngrid;
+}
+
+// One CTA per (grid, class).  With a tag that already holds `want` (a cached
+// schedule of this geometry) every CTA returns at once.
 template <int N>
-__global__ void __launch_bounds__(256) scatter_schedule_kernel(int V, unsigned short* __restrict__ sched) {
+__global__ void __launch_bounds__(256) scatter_schedule_kernel(int V, unsigned short* __restrict__ sched,
+                                                               const unsigned long long* tag,
+                                                               unsigned long long want) {
     using S = SchedShape<N>;
+    if (tag != nullptr && *reinterpret_cast<const volatile unsigned long long*>(tag) == want) return;
     constexpr int P = N + 1, WP = N + 1;
     const int gi = blockIdx.x / 9, cls = blockIdx.x % 9;
     const int pk = cls / 3, pb = cls % 3;
@@ -170,16 +182,25 @@ __global__ void __launch_bounds__(256) scatter_schedule_kernel(int V, unsigned s
 }
 
 // Launch the schedule builder for a one-CTA configuration (images up to
-// 128 x 128): ngrid x 9 CTAs.
-inline int sched_launch(int n, int V, int ngrid, unsigned short* sched, cudaStream_t st) {
+// 128 x 128): ngrid x 9 CTAs (skipped on the device when *tag == want).
+inline int sched_launch(int n, int V, int ngrid, unsigned short* sched, cudaStream_t st,
+                        const unsigned long long* tag = nullptr, unsigned long long want = 0) {
     switch (n) {
-        case 64: scatter_schedule_kernel<64><<<ngrid * 9, 256, 0, st>>>(V, sched); break;
-        case 96: scatter_schedule_kernel<96><<<ngrid * 9, 256, 0, st>>>(V, sched); break;
-        case 128: scatter_schedule_kernel<128><<<ngrid * 9, 256, 0, st>>>(V, sched); break;
+        case 64: scatter_schedule_kernel<64><<<ngrid * 9, 256, 0, st>>>(V, sched, tag, want); break;
+        case 96: scatter_schedule_kernel<96><<<ngrid * 9, 256, 0, st>>>(V, sched, tag, want); break;
+        case 128: scatter_schedule_kernel<128><<<ngrid * 9, 256, 0, st>>>(V, sched, tag, want); break;
         default: return BOAC_OK;
     }
     return launch_status();
 }
+
+// The schedule of geometry (n, V, ngrid) for a launch on stream st: a slot
+// of the device-side cache (built there when its tag does not name the
+// geometry), or, when no slot is free or the schedule is larger than a
+// slot, built into ws (sched_bytes(n, ngrid) bytes of the caller's
+// workspace).  Returns the schedule's address; *status is BOAC_OK or the
+// launch error.
+const unsigned short* sched_prepare(int n, int V, int ngrid, unsigned short* ws, cudaStream_t st, int* status);
 
 // A thread's words of one class of a grid's schedule (word t = tid + i NT:
 // warp w's lanes hold rounds 2 (w + i NT / 32) and that + 1).
