@@ -158,6 +158,12 @@ __global__ void __launch_bounds__(8 * N, 1) grad_fused_kernel(GradFusedArgs a) {
     auto project_grid = [&](int gi, const float* S, float* bf) {
         const float cs = csn[2 * gi], sn = csn[2 * gi + 1];
         const float* Xc = tab + (gi - g0) * gstride;
+        {   // the next grid's exponent planes: start their read from DRAM now
+            const int gn = gi + 1 < g1 ? gi + 1 : g0;
+            const float* nxt = tab + (gn - g0) * gstride;
+            constexpr int kLines = (int)((2 * (size_t)NN * sizeof(float) + 127) / 128);
+            for (int l = tid; l < kLines; l += NT) prefetch_l2(nxt + 32 * l);
+        }
         const float* XrT = Xc + NN;
         const float* Uc = Xc + 2 * NN;
         const float* Ur = Uc + N;
@@ -542,6 +548,11 @@ __global__ void __launch_bounds__(8 * N, 1) grad_fused_kernel(GradFusedArgs a) {
                 }
                 cluster_sync();
                 for (int gi = g0; gi < g1; ++gi) {
+                    {   // this grid's B F^n samples, read by mubar_grid below
+                        const float* yb = segB + ((size_t)t * ngrid + gi) * NN;
+                        constexpr int kLinesY = (int)(((size_t)NN * sizeof(float) + 127) / 128);
+                        for (int l = tid; l < kLinesY; l += NT) prefetch_l2(yb + 32 * l);
+                    }
                     project_grid(gi, S, nullptr);  // W <- B zbar, qv <- A zbar (rbar)
                     for (int u = tid; u < 4 * N; u += NT) {
                         const float q = __ldcg(segq + ((size_t)t * ngrid + gi) * 4 * N + u), s = Sg[u];
