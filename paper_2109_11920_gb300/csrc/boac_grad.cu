@@ -246,10 +246,11 @@ __global__ void mlem_step_adjoint_kernel(long long count, const float* __restric
 // gradient does not depend on the batch) into part_out[cand][h][NP], and
 // grad_coef_sum_kernel adds the parts in order.
 constexpr int kCoefParts = 8;
+// pg: the pixel geometry (r, P_1..P_5 per pixel, pixel_geom_launch).
 template <int NP>
 __global__ void grad_coef_kernel(int n, double dx, double mu_b0, double mu_c0, double dR0,
                                  const float* __restrict__ coef, const float* __restrict__ mubar,
-                                 double* __restrict__ part_out) {
+                                 const double* __restrict__ pg, double* __restrict__ part_out) {
     __shared__ double part[32][NP];
     const int cand = blockIdx.x, h = blockIdx.y;
     const int chunk = (n * n + kCoefParts - 1) / kCoefParts;
@@ -267,18 +268,14 @@ __global__ void grad_coef_kernel(int n, double dx, double mu_b0, double mu_c0, d
     double acc[NP];
 #pragma unroll
     for (int k = 0; k < NP; ++k) acc[k] = 0.0;
-    const double cc = 0.5 * (double)(n - 1);
     const float* mb = mubar + (size_t)cand * n * n;
+    const size_t nn = (size_t)n * n;
     for (int pix = p0 + threadIdx.x; pix < p1; pix += blockDim.x) {
-        const int i = pix / n, j = pix % n;
-        const double x = ((double)j - cc) * dx, y = ((double)i - cc) * dx;
-        const double r = sqrt(x * x + y * y);
-        const double z = r > 0.0 ? x / r : 1.0;
+        const double r = __ldg(pg + pix);
         double P[6];
         P[0] = 1.0;
-        P[1] = z;
 #pragma unroll
-        for (int k = 1; k < 5; ++k) P[k + 1] = ((2 * k + 1) * z * P[k] - k * P[k - 1]) / (k + 1);
+        for (int k = 1; k < 6; ++k) P[k] = __ldg(pg + k * nn + pix);
         double R = 0.0;
 #pragma unroll
         for (int k = 0; k < 6; ++k) R += c6[k] * P[k];
@@ -325,21 +322,31 @@ __global__ void grad_coef_sum_kernel(int B, const double* __restrict__ part, dou
     grad[i] = t;
 }
 
+// Doubles of coef_launch's scratch: the pixel geometry, then the parts.
+static size_t coef_scratch_doubles(const boac_geom* g, int B) {
+    return 6 * (size_t)g->n * g->n + (size_t)B * kCoefParts * kParams;
+}
+
 // mubar -> dL/dc (t != nullptr: c[B][6] with t's tissue values) or dL/dp
-// (t == nullptr: p[B][9]); part: B * kCoefParts * kParams doubles.
-static void coef_launch(const boac_geom* g, const boac_tissue* t, const float* c, const float* mubar, int B,
-                        double* part, double* dL_dc, cudaStream_t st) {
+// (t == nullptr: p[B][9]); scratch: coef_scratch_doubles(g, B) doubles.
+static int coef_launch(const boac_geom* g, const boac_tissue* t, const float* c, const float* mubar, int B,
+                       double* scratch, double* dL_dc, cudaStream_t st) {
     const int n = g->n;
     const double dx = (double)g->pixel_cm;
+    double* pg = scratch;
+    double* part = scratch + 6 * (size_t)n * n;
+    const int s = pixel_geom_launch(n, dx, pg, st);
+    if (s != BOAC_OK) return s;
     const dim3 grid((unsigned)B, kCoefParts);
     if (t) {
         grad_coef_kernel<6><<<grid, 256, 0, st>>>(n, dx, (double)t->mu_b, (double)t->mu_c, (double)t->dR, c, mubar,
-                                                  part);
+                                                  pg, part);
         grad_coef_sum_kernel<6><<<(B * 6 + 255) / 256, 256, 0, st>>>(B, part, dL_dc);
     } else {
-        grad_coef_kernel<kParams><<<grid, 256, 0, st>>>(n, dx, 0.0, 0.0, 0.0, c, mubar, part);
+        grad_coef_kernel<kParams><<<grid, 256, 0, st>>>(n, dx, 0.0, 0.0, 0.0, c, mubar, pg, part);
         grad_coef_sum_kernel<kParams><<<(B * kParams + 255) / 256, 256, 0, st>>>(B, part, dL_dc);
     }
+    return launch_status();
 }
 
 // ------------------------------------------------------------- workspace
@@ -379,7 +386,7 @@ static GradLayout grad_layout(const boac_geom* g, int B, int K, int ckpt) {
     L.rbar = take(Bs * vb);
     L.partial = take(bp_partial_floats(g, B));
     L.lg = take(2 * kLgammaScratchDoubles);  // the ln S! sum of a shared sinogram
-    L.coefp = take(2 * Bs * kCoefParts * kParams);  // doubles
+    L.coefp = take(2 * coef_scratch_doubles(g, B));  // doubles
     L.total = off;
     return L;
 }
@@ -418,7 +425,7 @@ static GradFusedLayout grad_fused_layout(const boac_geom* g, int B, int K, int c
     L.abar = take(Bs * (size_t)(g->n_views / 4) * nn);
     L.mubar = take(Bs * nn);
     L.lg = take(2 * kLgammaScratchDoubles);
-    L.coefp = take(2 * Bs * kCoefParts * kParams);  // doubles
+    L.coefp = take(2 * coef_scratch_doubles(g, B));  // doubles
     L.sched = off;
     off += sched_bytes(g->n, g->n_views / 4);
     L.total = off;
@@ -472,8 +479,7 @@ static int score_grad_fused_run(const boac_geom* g, const boac_tissue* t, const 
     s = grad_fused_launch(g, a, G, holders, st);
     if (s != BOAC_OK) return s;
     phase.next("gradient (fused): pixels -> coefficients");
-    coef_launch(g, t, c, P(lay.mubar), B, reinterpret_cast<double*>(base + lay.coefp), dL_dc, st);
-    return launch_status();
+    return coef_launch(g, t, c, P(lay.mubar), B, reinterpret_cast<double*>(base + lay.coefp), dL_dc, st);
 }
 
 // The path boac_score_grad takes: the fused kernel where it applies (G > 0).
@@ -606,8 +612,7 @@ static int score_grad_run(const boac_geom* g, const boac_tissue* t, const float*
     // attenuation -> mu samples -> pixels -> coefficients
     mbar_kernel<<<rg, kRayThreads, 0, st>>>(n, V, dx, tab, abar);
     backproject_table(g, B, abar, nullptr, 1.0f, mubar, 0, partial, st);
-    coef_launch(g, t, c, mubar, B, reinterpret_cast<double*>(base + lay.coefp), dL_dc, st);
-    return launch_status();
+    return coef_launch(g, t, c, mubar, B, reinterpret_cast<double*>(base + lay.coefp), dL_dc, st);
 }
 
 extern "C" int boac_score_grad(const boac_geom* g, const boac_tissue* t, const float* c,

@@ -86,5 +86,8 @@ constexpr int kParams = 9;
 // 6 takes the tissue values from t, pstride kParams from p (t unused).
 int rasterize_launch(const boac_geom* g, const boac_tissue* t, const float* p, int pstride, int B,
                      int mode, float* mu, cudaStream_t st);
+// The pixel geometry of the n x n grid: pg[0][pix] = r, pg[k][pix] =
+// P_k(cos theta), k = 1..5 (6 n^2 doubles).
+int pixel_geom_launch(int n, double dx, double* pg, cudaStream_t st);
 
 }  // namespace boac
