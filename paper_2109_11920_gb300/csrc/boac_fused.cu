@@ -68,6 +68,7 @@ struct FusedShape {
 //   Uc[b]    = whole-column sum: the view phi + pi exponent is Uc - Xc
 //   XrT[b][k] = view phi + pi/2 (detector at b -> -inf, prefix along b),
 //               stored transposed for row-parallel access
+// (the planes in the interleaved order of tab_ix below)
 //   Ur[k]    = whole-row sum: the view phi + 3pi/2 exponent is Ur - XrT
 // because for one ray the half-cell sums towards both ends add up to the
 // ray's total: a_phi * a_{phi+pi} = exp(-dx sum_k mu_k).
@@ -256,7 +257,7 @@ __global__ void __launch_bounds__(NT, (G > 1 ? 1 : fused_min_blocks<N, NT>())) m
                 for (int s = SEG - 1; s >= 0; --s) {
                     const int k = k0 + s;
                     const float m = W[k * WP + lb];
-                    Xc[k * N + lb] = ndl * (0.5f * m + suf);
+                    Xc[tab_ix(N, k, lb)] = ndl * (0.5f * m + suf);
                     suf += m;
                 }
                 if (seg == 0) Uc[lb] = ndl * total;
@@ -279,7 +280,7 @@ __global__ void __launch_bounds__(NT, (G > 1 ? 1 : fused_min_blocks<N, NT>())) m
                 for (int s = 0; s < SEG; ++s) {
                     const int b = k0 + s;
                     const float m = W[lb * WP + b];
-                    XrT[b * N + lb] = ndl * (0.5f * m + pre);
+                    XrT[tab_ix(N, b, lb)] = ndl * (0.5f * m + pre);
                     pre += m;
                 }
                 if (seg == 0) Ur[lb] = ndl * total;
@@ -290,7 +291,7 @@ __global__ void __launch_bounds__(NT, (G > 1 ? 1 : fused_min_blocks<N, NT>())) m
 #pragma unroll 8
                 for (int s = 0; s < SEG; ++s) {
                     const int k = k0 + s;
-                    const float y = Xc[k * N + lb];
+                    const float y = Xc[tab_ix(N, k, lb)];
                     W[k * WP + lb] = dx * (ex2(y) + ex2(uc - y));
                 }
             }
@@ -300,7 +301,7 @@ __global__ void __launch_bounds__(NT, (G > 1 ? 1 : fused_min_blocks<N, NT>())) m
 #pragma unroll 8
                 for (int s = 0; s < SEG; ++s) {
                     const int b = k0 + s;
-                    const float y = XrT[b * N + lb];
+                    const float y = XrT[tab_ix(N, b, lb)];
                     W[lb * WP + b] += dx * (ex2(y) + ex2(ur - y));
                 }
             }
@@ -391,16 +392,20 @@ __global__ void __launch_bounds__(NT, (G > 1 ? 1 : fused_min_blocks<N, NT>())) m
                 {
                     const float uc = Uc[lb];
                     float acc1 = 0.0f, acc2 = 0.0f;
-#pragma unroll 8
-                    for (int s = 0; s < SEG; ++s) {
-                        const int k = k0 + s;
-                        float u, w;
-                        sample_uw(k, lb, cs, sn, c, &u, &w);
-                        const float f = bilerp_padded(img0, P, N, u, w);
-                        if (QUAD) W[k * WP + lb] = f;
-                        const float y = Xc[k * N + lb];
-                        acc1 = fmaf(ex2(y), f, acc1);
-                        acc2 = fmaf(ex2(uc - y), f, acc2);
+#pragma unroll 2
+                    for (int s4 = 0; s4 < SEG; s4 += 4) {
+                        const float4 y4 = *reinterpret_cast<const float4*>(Xc + tab_ix(N, k0 + s4, lb));
+                        const float yy[4] = {y4.x, y4.y, y4.z, y4.w};
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const int k = k0 + s4 + j;
+                            float u, w;
+                            sample_uw(k, lb, cs, sn, c, &u, &w);
+                            const float f = bilerp_padded(img0, P, N, u, w);
+                            if (QUAD) W[k * WP + lb] = f;
+                            acc1 = fmaf(ex2(yy[j]), f, acc1);
+                            acc2 = fmaf(ex2(uc - yy[j]), f, acc2);
+                        }
                     }
                     redc[seg * N + lb] = acc1;
                     redc[(NSEG + seg) * N + lb] = acc2;
@@ -409,13 +414,16 @@ __global__ void __launch_bounds__(NT, (G > 1 ? 1 : fused_min_blocks<N, NT>())) m
                     __syncthreads();
                     const float ur = Ur[lb];
                     float acc3 = 0.0f, acc4 = 0.0f;
-#pragma unroll 8
-                    for (int s = 0; s < SEG; ++s) {
-                        const int b = k0 + s;
-                        const float f = W[lb * WP + b];
-                        const float y = XrT[b * N + lb];
-                        acc3 = fmaf(ex2(y), f, acc3);
-                        acc4 = fmaf(ex2(ur - y), f, acc4);
+#pragma unroll 2
+                    for (int s4 = 0; s4 < SEG; s4 += 4) {
+                        const float4 y4 = *reinterpret_cast<const float4*>(XrT + tab_ix(N, k0 + s4, lb));
+                        const float yy[4] = {y4.x, y4.y, y4.z, y4.w};
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const float f = W[lb * WP + k0 + s4 + j];
+                            acc3 = fmaf(ex2(yy[j]), f, acc3);
+                            acc4 = fmaf(ex2(ur - yy[j]), f, acc4);
+                        }
                     }
                     redr[seg * N + lb] = acc3;
                     redr[(NSEG + seg) * N + lb] = acc4;
@@ -442,21 +450,25 @@ __global__ void __launch_bounds__(NT, (G > 1 ? 1 : fused_min_blocks<N, NT>())) m
                 {
                     const float uc = Uc[lb];
                     const float r1 = dx * rr[lb], r2 = dx * rr[N + lb];
-#pragma unroll 8
-                    for (int s = 0; s < SEG; ++s) {
-                        const int k = k0 + s;
-                        const float y = Xc[k * N + lb];
-                        W[k * WP + lb] = fmaf(ex2(y), r1, ex2(uc - y) * r2);
+#pragma unroll 2
+                    for (int s4 = 0; s4 < SEG; s4 += 4) {
+                        const float4 y4 = *reinterpret_cast<const float4*>(Xc + tab_ix(N, k0 + s4, lb));
+                        const float yy[4] = {y4.x, y4.y, y4.z, y4.w};
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            W[(k0 + s4 + j) * WP + lb] = fmaf(ex2(yy[j]), r1, ex2(uc - yy[j]) * r2);
                     }
                 }
                 if (QUAD) {
                     __syncthreads();
                     const float ur = Ur[lb];
                     const float r3 = dx * rr[2 * N + lb], r4 = dx * rr[3 * N + lb];
-                    for (int s = 0; s < SEG; ++s) {
-                        const int b = k0 + s;
-                        const float y = XrT[b * N + lb];
-                        W[lb * WP + b] += fmaf(ex2(y), r3, ex2(ur - y) * r4);
+                    for (int s4 = 0; s4 < SEG; s4 += 4) {
+                        const float4 y4 = *reinterpret_cast<const float4*>(XrT + tab_ix(N, k0 + s4, lb));
+                        const float yy[4] = {y4.x, y4.y, y4.z, y4.w};
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            W[lb * WP + k0 + s4 + j] += fmaf(ex2(yy[j]), r3, ex2(ur - yy[j]) * r4);
                     }
                 }
                 __syncthreads();

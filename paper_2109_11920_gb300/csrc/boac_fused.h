@@ -93,6 +93,13 @@ __device__ __forceinline__ void copy_async_commit() { asm volatile("cp.async.com
 __device__ __forceinline__ void copy_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Ask L2 to fetch the 128-byte line holding p (no register result).
+// Exponent planes keep four consecutive samples of a thread's run
+// together: element (k, b) of a plane walked by thread b along k (or (b, k)
+// of a transposed plane walked by thread k along b) at ((k / 4) n + b) 4 +
+// k % 4, so one 16-byte load gives a thread its next four samples and a
+// warp's load covers 512 contiguous bytes.
+__host__ __device__ constexpr int tab_ix(int n, int k, int lb) { return (((k >> 2) * n + lb) << 2) | (k & 3); }
+
 __device__ __forceinline__ void prefetch_l2(const void* p) {
     asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }

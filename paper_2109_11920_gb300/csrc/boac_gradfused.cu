@@ -176,19 +176,22 @@ __global__ void __launch_bounds__(8 * N, 1) grad_fused_kernel(GradFusedArgs a) {
             const float uc = Uc[lb];
             float acc1 = 0.0f, acc2 = 0.0f;
             float fq[4];
-#pragma unroll 8
-            for (int s = 0; s < SEG; ++s) {
-                const int k = k0 + s;
-                float u, w;
-                sample_uw(k, lb, cs, sn, c, &u, &w);
-                const float f = bilerp_padded(img0, P, N, u, w);
-                W[k * WP + lb] = f;
-                fq[s & 3] = f;  // bf: sample (k, b) at b n + k, four k per store, read once
-                if ((s & 3) == 3 && bf)
-                    __stcs(reinterpret_cast<float4*>(bf + lb * N + k - 3), make_float4(fq[0], fq[1], fq[2], fq[3]));
-                const float y = Xc[k * N + lb];
-                acc1 = fmaf(ex2(y), f, acc1);
-                acc2 = fmaf(ex2(uc - y), f, acc2);
+#pragma unroll 2
+            for (int s4 = 0; s4 < SEG; s4 += 4) {
+                const float4 y4 = *reinterpret_cast<const float4*>(Xc + tab_ix(N, k0 + s4, lb));
+                const float yy[4] = {y4.x, y4.y, y4.z, y4.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int k = k0 + s4 + j;
+                    float u, w;
+                    sample_uw(k, lb, cs, sn, c, &u, &w);
+                    const float f = bilerp_padded(img0, P, N, u, w);
+                    W[k * WP + lb] = f;
+                    fq[j] = f;  // bf: sample (k, b) at b n + k, four k per store, read once
+                    acc1 = fmaf(ex2(yy[j]), f, acc1);
+                    acc2 = fmaf(ex2(uc - yy[j]), f, acc2);
+                }
+                if (bf) __stcs(reinterpret_cast<float4*>(bf + lb * N + k0 + s4), make_float4(fq[0], fq[1], fq[2], fq[3]));
             }
             redc[seg * N + lb] = acc1;
             redc[(NSEG + seg) * N + lb] = acc2;
@@ -197,13 +200,16 @@ __global__ void __launch_bounds__(8 * N, 1) grad_fused_kernel(GradFusedArgs a) {
         {
             const float ur = Ur[lb];
             float acc3 = 0.0f, acc4 = 0.0f;
-#pragma unroll 8
-            for (int s = 0; s < SEG; ++s) {
-                const int b = k0 + s;
-                const float f = W[lb * WP + b];
-                const float y = XrT[b * N + lb];
-                acc3 = fmaf(ex2(y), f, acc3);
-                acc4 = fmaf(ex2(ur - y), f, acc4);
+#pragma unroll 2
+            for (int s4 = 0; s4 < SEG; s4 += 4) {
+                const float4 y4 = *reinterpret_cast<const float4*>(XrT + tab_ix(N, k0 + s4, lb));
+                const float yy[4] = {y4.x, y4.y, y4.z, y4.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float f = W[lb * WP + k0 + s4 + j];
+                    acc3 = fmaf(ex2(yy[j]), f, acc3);
+                    acc4 = fmaf(ex2(ur - yy[j]), f, acc4);
+                }
             }
             redr[seg * N + lb] = acc3;
             redr[(NSEG + seg) * N + lb] = acc4;
@@ -251,11 +257,13 @@ __global__ void __launch_bounds__(8 * N, 1) grad_fused_kernel(GradFusedArgs a) {
                 const float4 y4 = Y ? __ldcg(reinterpret_cast<const float4*>(Yc + lb * N + k0 + s4))
                                     : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
                 const float yy[4] = {y4.x, y4.y, y4.z, y4.w};
+                const float4 e4 = *reinterpret_cast<const float4*>(Xc + tab_ix(N, k0 + s4, lb));
+                const float ee[4] = {e4.x, e4.y, e4.z, e4.w};
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const int k = k0 + s4 + j;
                     const float x = W[k * WP + lb];
-                    const float ye = Xc[k * N + lb];
+                    const float ye = ee[j];
                     const float a1 = ex2(ye) * fmaf(w21, yy[j], w11 * x);
                     const float a2 = ex2(uc - ye) * fmaf(w22, yy[j], w12 * x);
                     q2 += a2;
@@ -273,17 +281,22 @@ __global__ void __launch_bounds__(8 * N, 1) grad_fused_kernel(GradFusedArgs a) {
             const float w13 = dx * k1[2 * N + k], w14 = dx * k1[3 * N + k];
             const float w23 = Y ? dx * k2[2 * N + k] : 0.0f, w24 = Y ? dx * k2[3 * N + k] : 0.0f;
             float q3 = 0.0f, p4 = 0.0f;
-#pragma unroll 4
-            for (int s = 0; s < SEG; ++s) {
-                const int b = k0 + s;
-                const float x = W[k * WP + b];
-                const float yv = Y ? __ldcg(Yc + b * N + k) : 0.0f;
-                const float ye = XrT[b * N + k];
-                const float a3 = ex2(ye) * fmaf(w23, yv, w13 * x);
-                const float a4 = ex2(ur - ye) * fmaf(w24, yv, w14 * x);
-                q3 += a3;
-                W[k * WP + b] = fmaf(0.5f, a3 + a4, p4 - q3);  // + a3 of the segment
-                p4 += a4;
+#pragma unroll 1
+            for (int s4 = 0; s4 < SEG; s4 += 4) {
+                const float4 e4 = *reinterpret_cast<const float4*>(XrT + tab_ix(N, k0 + s4, k));
+                const float ee[4] = {e4.x, e4.y, e4.z, e4.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int b = k0 + s4 + j;
+                    const float x = W[k * WP + b];
+                    const float yv = Y ? __ldcg(Yc + b * N + k) : 0.0f;
+                    const float ye = ee[j];
+                    const float a3 = ex2(ye) * fmaf(w23, yv, w13 * x);
+                    const float a4 = ex2(ur - ye) * fmaf(w24, yv, w14 * x);
+                    q3 += a3;
+                    W[k * WP + b] = fmaf(0.5f, a3 + a4, p4 - q3);  // + a3 of the segment
+                    p4 += a4;
+                }
             }
             redr[seg * N + k] = q3;
             redr[(NSEG + seg) * N + k] = p4;
@@ -323,21 +336,23 @@ __global__ void __launch_bounds__(8 * N, 1) grad_fused_kernel(GradFusedArgs a) {
         {
             const float uc = Uc[lb];
             const float r1 = dx * kc[lb], r2 = dx * kc[N + lb];
-#pragma unroll 8
-            for (int s = 0; s < SEG; ++s) {
-                const int k = k0 + s;
-                const float y = Xc[k * N + lb];
-                W[k * WP + lb] = fmaf(ex2(y), r1, ex2(uc - y) * r2);
+#pragma unroll 2
+            for (int s4 = 0; s4 < SEG; s4 += 4) {
+                const float4 y4 = *reinterpret_cast<const float4*>(Xc + tab_ix(N, k0 + s4, lb));
+                const float yy[4] = {y4.x, y4.y, y4.z, y4.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) W[(k0 + s4 + j) * WP + lb] = fmaf(ex2(yy[j]), r1, ex2(uc - yy[j]) * r2);
             }
         }
         __syncthreads();
         {
             const float ur = Ur[lb];
             const float r3 = dx * kc[2 * N + lb], r4 = dx * kc[3 * N + lb];
-            for (int s = 0; s < SEG; ++s) {
-                const int b = k0 + s;
-                const float y = XrT[b * N + lb];
-                W[lb * WP + b] += fmaf(ex2(y), r3, ex2(ur - y) * r4);
+            for (int s4 = 0; s4 < SEG; s4 += 4) {
+                const float4 y4 = *reinterpret_cast<const float4*>(XrT + tab_ix(N, k0 + s4, lb));
+                const float yy[4] = {y4.x, y4.y, y4.z, y4.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) W[lb * WP + k0 + s4 + j] += fmaf(ex2(yy[j]), r3, ex2(ur - yy[j]) * r4);
             }
         }
         __syncthreads();
@@ -398,7 +413,7 @@ __global__ void __launch_bounds__(8 * N, 1) grad_fused_kernel(GradFusedArgs a) {
                 for (int s = SEG - 1; s >= 0; --s) {
                     const int k = k0 + s;
                     const float m = W[k * WP + lb];
-                    Xc[k * N + lb] = ndl * (0.5f * m + suf);
+                    Xc[tab_ix(N, k, lb)] = ndl * (0.5f * m + suf);
                     suf += m;
                 }
                 if (seg == 0) Uc[lb] = ndl * total;
@@ -421,7 +436,7 @@ __global__ void __launch_bounds__(8 * N, 1) grad_fused_kernel(GradFusedArgs a) {
                 for (int s = 0; s < SEG; ++s) {
                     const int b = k0 + s;
                     const float m = W[lb * WP + b];
-                    XrT[b * N + lb] = ndl * (0.5f * m + pre);
+                    XrT[tab_ix(N, b, lb)] = ndl * (0.5f * m + pre);
                     pre += m;
                 }
                 if (seg == 0) Ur[lb] = ndl * total;
