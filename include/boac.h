@@ -26,6 +26,11 @@
  *     row-major float32 (or float64 where stated) memory on the current CUDA
  *     device.  The library allocates no device memory: operations that need
  *     scratch take a caller-allocated workspace (see boac_workspace_bytes).
+ *     It holds two arrays of static device memory on every GPU that loads
+ *     it: the 64 MiB scratch of boac_mlem_noalloc and 32 MiB of scatter
+ *     schedules kept across calls for up to 8 geometries (the fused kernels
+ *     build a geometry's schedule once; later geometries build it in the
+ *     workspace on every call).
  *   - Work is enqueued asynchronously on `stream` (a cudaStream_t; NULL =
  *     the legacy default stream).  Return values report argument and launch
  *     errors only; kernel faults surface at the next synchronisation.
@@ -220,13 +225,15 @@ int boac_backproject(const boac_geom *g, const float *mu, const float *y,
  *   K        iterations (>= 0)
  *   L        [B] float64 output, or NULL to skip the score
  * boac_mlem is the batched path: one persistent fused kernel runs every
- * iteration of every candidate on chip (n <= 128: one CTA per candidate;
- * n = 256 with n_views % 4 == 0, and n = 128 with n_views % 4 == 0 when B
- * is too small to give every SM a candidate: a thread-block cluster per
- * candidate, the image split into bands of rows over its CTAs); batches
- * too small to fill the GPU that way (at most 32 candidates at n = 64 and
- * 96, 16 at 128, 2 at 256, scaled by the SM count / 152) run the unfused
- * batched kernels of boac_mlem_unfused instead.  The choice depends on B,
+ * iteration of every candidate on chip.  n <= 128: one CTA per candidate,
+ * or, with n_views % 4 == 0 where a cost model over the resident cluster
+ * counts finds it faster (batches that cannot give every SM a candidate),
+ * a thread-block cluster of 2 to 16 CTAs per candidate, each CTA on a share
+ * of the sample grids; n = 256 with n_views % 4 == 0: a cluster per
+ * candidate with the image split into bands of rows over its CTAs.
+ * Batches too small to fill the GPU that take neither cluster form (at
+ * most 32 candidates at n = 64 and 96, 16 at 128, 2 at 256, scaled by the
+ * SM count / 152) run the unfused batched kernels of boac_mlem_unfused.  The choice depends on B,
  * so query the workspace with the same B.  boac_mlem_plain is the
  * launch-per-step path: one candidate at a time, separate project / ratio /
  * backproject / update kernels per iteration (the comparison baseline).
