@@ -31,6 +31,25 @@ def probs():
     return {s: make_problem(*s, counts=2e5, B=3, seed=11) for s in SHAPES + ODD}
 
 
+@pytest.mark.parametrize("mode", [oracle.CENTER, oracle.AREA])
+def test_rasterize_candidate_groups(cuda, mode):
+    """The rasteriser takes a pixel for a group of 8 candidates: 19
+    candidates (two full groups and a ragged one) against the oracle, and
+    bit for bit against rasterising each candidate alone."""
+    p = make_problem(64, 0.4, 60, 1e5, B=19, seed=5, mode=mode)
+    g, t = geom(p), Tissue(*p.tissue)
+    mu = boac.boac_rasterize_mu(g, t, T(p.coefs, cuda), mode)
+    for b in range(19):
+        one = boac.boac_rasterize_mu(g, t, T(p.coefs[b:b + 1], cuda), mode)
+        assert torch.equal(mu[b], one[0]), b
+    mu = mu.cpu().numpy()
+    for b in range(19):
+        if mode == oracle.CENTER:
+            assert_center_classes(mu[b], p.mu[b], p.n, p.dx, p.coefs[b], p.tissue[2])
+        else:
+            np.testing.assert_allclose(mu[b], p.mu[b], rtol=1e-6, atol=1e-7, err_msg=str(b))
+
+
 @pytest.mark.parametrize("shape", SHAPES)
 @pytest.mark.parametrize("mode", [oracle.CENTER, oracle.AREA])
 def test_rasterize(cuda, shape, mode):
