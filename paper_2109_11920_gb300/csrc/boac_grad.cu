@@ -155,20 +155,6 @@ __global__ void mbar_kernel(int n, int V, float dx, const float* __restrict__ ta
     }
 }
 
-// The same scan of an abar already multiplied by the factors (the fused
-// gradient kernel accumulates abar * a): mbar_k = -dx (x_k / 2 + sum_{k'<k} x_k').
-__global__ void mbar_scan_kernel(int n, int V, float dx, float* __restrict__ abar) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x, v = blockIdx.y, cand = blockIdx.z;
-    if (b >= n) return;
-    const size_t nn = (size_t)n * n;
-    float* ab = abar + ((size_t)cand * V + v) * nn;
-    float prefix = 0.0f;
-    for (int k = 0; k < n; ++k) {
-        const float aa = ab[(size_t)k * n + b];
-        ab[(size_t)k * n + b] = -dx * (0.5f * aa + prefix);
-        prefix += aa;
-    }
-}
 
 __global__ void fill_ones_kernel(long long count, float* __restrict__ x) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
