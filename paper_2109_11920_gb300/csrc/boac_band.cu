@@ -906,3 +906,9 @@ int band_launch(int n, int nb, const FusedArgs& a, int clusters, cudaStream_t st
 #undef BOAC_BAND_CASES
 
 }  // namespace boac
+
+#ifdef BOAC_CHECKED
+namespace boac {
+BOAC_FAULT_READER(bounds_faults_band)
+}  // namespace boac
+#endif

@@ -75,9 +75,17 @@ extern "C" int boac_abi_version(void) { return 1; }
 extern "C" int boac_bounds_faults(int* faults, int reset) {
 #ifdef BOAC_CHECKED
     if (!faults) return BOAC_EINVAL;
-    const int f = bounds_faults_fused(reset), b = bounds_faults_bpgroup(reset);
-    if (f < 0 || b < 0) return BOAC_ECUDA;
-    *faults = f + b;
+    // one counter per translation unit that uses the checked helpers
+    int (*const readers[])(int) = {bounds_faults_fused,   bounds_faults_bpgroup, bounds_faults_gradfused,
+                                   bounds_faults_grad,    bounds_faults_plain,   bounds_faults_unfused,
+                                   bounds_faults_sysmat,  bounds_faults_band,    bounds_faults_raster};
+    int total = 0;
+    for (int (*r)(int) : readers) {
+        const int v = r(reset);
+        if (v < 0) return BOAC_ECUDA;
+        total += v;
+    }
+    *faults = total;
     return BOAC_OK;
 #else
     (void)faults;

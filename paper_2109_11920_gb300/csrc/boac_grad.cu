@@ -636,3 +636,9 @@ extern "C" int boac_score_grad_params(const boac_geom* g, const float* p, const 
     return score_grad_run(g, nullptr, p, S, s_stride, K, ckpt_every, B, include_lgamma, L, dL_dp,
                           F_out, ws, ws_bytes, stream);
 }
+
+#ifdef BOAC_CHECKED
+namespace boac {
+BOAC_FAULT_READER(bounds_faults_grad)
+}  // namespace boac
+#endif

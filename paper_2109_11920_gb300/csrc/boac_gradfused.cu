@@ -770,3 +770,9 @@ int grad_fused_launch(const boac_geom* g, const GradFusedArgs& args, int G, int 
 }
 
 }  // namespace boac
+
+#ifdef BOAC_CHECKED
+namespace boac {
+BOAC_FAULT_READER(bounds_faults_gradfused)
+}  // namespace boac
+#endif

@@ -61,6 +61,13 @@ struct NvtxPhases {
 // the read failed; reset clears the counter).
 int bounds_faults_fused(int reset);
 int bounds_faults_bpgroup(int reset);
+int bounds_faults_gradfused(int reset);
+int bounds_faults_grad(int reset);
+int bounds_faults_plain(int reset);
+int bounds_faults_unfused(int reset);
+int bounds_faults_sysmat(int reset);
+int bounds_faults_band(int reset);
+int bounds_faults_raster(int reset);
 #endif
 
 // Round up to a multiple of 256 bytes.

@@ -326,3 +326,9 @@ extern "C" int boac_mlem_plain(const boac_geom* g, const float* mu, const float*
     }
     return BOAC_OK;
 }
+
+#ifdef BOAC_CHECKED
+namespace boac {
+BOAC_FAULT_READER(bounds_faults_plain)
+}  // namespace boac
+#endif

@@ -149,3 +149,9 @@ extern "C" int boac_rasterize_mu_params(const boac_geom* g, const float* p, int 
     if (mode != BOAC_RASTER_CENTER && mode != BOAC_RASTER_AREA) return BOAC_EINVAL;
     return rasterize_launch(g, nullptr, p, kParams, B, mode, mu, as_stream(stream));
 }
+
+#ifdef BOAC_CHECKED
+namespace boac {
+BOAC_FAULT_READER(bounds_faults_raster)
+}  // namespace boac
+#endif

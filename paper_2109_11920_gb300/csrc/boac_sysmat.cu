@@ -671,3 +671,9 @@ extern "C" int boac_sysmat_mlem(const boac_sysmat* m, const float* vals, const f
     }
     return launch_status();
 }
+
+#ifdef BOAC_CHECKED
+namespace boac {
+BOAC_FAULT_READER(bounds_faults_sysmat)
+}  // namespace boac
+#endif

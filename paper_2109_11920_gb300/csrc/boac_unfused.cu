@@ -97,3 +97,9 @@ extern "C" int boac_mlem_unfused(const boac_geom* g, const float* mu, const floa
     if ((long long)B * g->n * g->n > 0x7fffffffLL) return BOAC_EINVAL;
     return mlem_unfused(g, mu, S, s_stride, F, K, B, L, include_lgamma, ws, ws_bytes, as_stream(stream));
 }
+
+#ifdef BOAC_CHECKED
+namespace boac {
+BOAC_FAULT_READER(bounds_faults_unfused)
+}  // namespace boac
+#endif

@@ -1,16 +1,19 @@
 """The bounds-checked build, libboac_checked.so (built here on demand with
 -DBOAC_CHECKED).  It runs boac_mlem's small-batch path (the unfused grouped
-kernels), the fused one-CTA kernel and its cluster mode on a small case
-through the C ABI: every checked shared-memory index and schedule entry is
-in range (fault count 0), and the results equal the normal build's bit for
-bit (the checks change no arithmetic)."""
+kernels), the fused one-CTA kernel and its cluster mode, and the score
+gradient (the fused gradient kernel and the batched reverse mode) on small
+cases through the C ABI: every checked shared-memory index and schedule
+entry is in range (fault count 0, summed over every translation unit), and
+the results equal the normal build's bit for bit (the checks change no
+arithmetic)."""
 import ctypes
 
 import numpy as np
 import pytest
 import torch
 
-from paper_2109_11920_gb300 import Geom, _lib
+import oracle
+from paper_2109_11920_gb300 import Geom, Tissue, _lib
 from paper_2109_11920_gb300 import api as boac
 from problems import make_problem
 
@@ -70,3 +73,44 @@ def test_checked_build_runs_clean_and_matches(cuda):
     for (Fr, Lr), (Fc, Lc) in zip(ref, got):
         np.testing.assert_array_equal(Fc, Fr)
         np.testing.assert_array_equal(Lc, Lr)
+
+
+def run_grad(lib, p, dev, K, ckpt):
+    """(L, dL/dc) of boac_score_grad (the fused gradient kernel) and of
+    boac_score_grad_unfused (the batched reverse mode), through `lib`."""
+    g = Geom.make(p.n, p.dx, p.V)
+    B = p.coefs.shape[0]
+    t = Tissue(*p.tissue)
+    c = torch.tensor(p.coefs, dtype=torch.float32, device=dev)
+    S = torch.tensor(p.S, dtype=torch.float32, device=dev)
+    nbytes = lib.boac_score_grad_workspace_bytes(ctypes.byref(g), B, K, ckpt)
+    assert nbytes > 0
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    out = []
+    for fn in (lib.boac_score_grad, lib.boac_score_grad_unfused):
+        L = torch.empty(B, dtype=torch.float64, device=dev)
+        G = torch.empty(B, 6, dtype=torch.float64, device=dev)
+        st = fn(ctypes.byref(g), ctypes.byref(t), _p(c), _p(S), 0, K, ckpt, B, 1, _p(L), _p(G), None,
+                _p(ws), nbytes, _stream())
+        assert st == _lib.BOAC_OK, _lib.status_string(st)
+        out.append((L.cpu().numpy(), G.cpu().numpy()))
+    torch.cuda.synchronize()
+    return out
+
+
+def test_checked_build_gradient(cuda):
+    from paper_2109_11920_gb300 import build
+    build.build()
+    build.build(checked=True)
+    norm, chk = _lib.load(), _lib.load_checked()
+    faults = ctypes.c_int(-1)
+    assert chk.boac_bounds_faults(ctypes.byref(faults), 1) == _lib.BOAC_OK
+    for n, dx, V in ((128, 0.2, 120), (96, 25.6 / 96, 92)):
+        p = make_problem(n, dx, V, 2e5, B=3, seed=31, mode=oracle.AREA)
+        ref = run_grad(norm, p, cuda, 3, 2)
+        got = run_grad(chk, p, cuda, 3, 2)
+        for (Lr, Gr), (Lc, Gc) in zip(ref, got):
+            np.testing.assert_array_equal(Lc, Lr)
+            np.testing.assert_array_equal(Gc, Gr)
+    assert chk.boac_bounds_faults(ctypes.byref(faults), 0) == _lib.BOAC_OK
+    assert faults.value == 0
