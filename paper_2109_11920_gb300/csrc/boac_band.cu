@@ -144,24 +144,29 @@ __device__ __forceinline__ int band_of_row(int fi) {
     return r;
 }
 
-// Bilinear sample / transposed scatter in a padded band image whose local
-// row 0 is image row R0 - 1; the sample is known to lie in the band.
-template <int P>
+// Bilinear sample / transposed scatter in a padded band image of BIMG
+// floats whose local row 0 is image row R0 - 1; the sample is known to lie
+// in the band (checked builds verify that the 2 x 2 footprint does).
+template <int P, int BIMG>
 __device__ __forceinline__ float bilerp_band(const float* img, int R0, float u, float w) {
     const float fj = floorf(u), fi = floorf(w);
     const float au = u - fj, aw = w - fi;
-    const float* p = img + ((int)fi - R0 + 1) * P + ((int)fj + 1);
+    const int idx = ((int)fi - R0 + 1) * P + ((int)fj + 1);
+    if (!index_ok(idx, (long long)BIMG - P - 1)) return 0.0f;
+    const float* p = img + idx;
     const float v00 = p[0], v01 = p[1], v10 = p[P], v11 = p[P + 1];
     const float top = fmaf(au, v01 - v00, v00);
     const float bot = fmaf(au, v11 - v10, v10);
     return fmaf(aw, bot - top, top);
 }
 
-template <int P>
+template <int P, int BIMG>
 __device__ __forceinline__ void scatter_band(float* img, int R0, float u, float w, float g) {
     const float fj = floorf(u), fi = floorf(w);
     const float au = u - fj, aw = w - fi;
-    float* p = img + ((int)fi - R0 + 1) * P + ((int)fj + 1);
+    const int idx = ((int)fi - R0 + 1) * P + ((int)fj + 1);
+    if (!index_ok(idx, (long long)BIMG - P - 1)) return;
+    float* p = img + idx;
     const float g1 = g * aw, g0 = g - g1;
     const float g01 = g0 * au, g00 = g0 - g01;
     const float g11 = g1 * au, g10 = g1 - g11;
@@ -287,7 +292,7 @@ __device__ __forceinline__ void band_scatter5(const float* W, float* Ab, const i
             const float g = W[(k - lo) * WP + b];
             float u, w;
             sample_uw(k, b, cs, sn, c, &u, &w);
-            scatter_band<P>(Ab, R0, u, w, g);
+            scatter_band<P, S::BIMG>(Ab, R0, u, w, g);
         }
         __syncthreads();
     }
@@ -316,7 +321,7 @@ __device__ __forceinline__ void band_scatter(const float* W, float* Ab, const in
                 const float g = W[(k - lo) * WP + b];
                 float u, w;
                 sample_uw(k, b, cs, sn, c, &u, &w);
-                scatter_band<P>(Ab, R0, u, w, g);
+                scatter_band<P, S::BIMG>(Ab, R0, u, w, g);
             }
         }
         __syncthreads();
@@ -471,7 +476,7 @@ __global__ void __launch_bounds__(4 * N, N == 64 ? 4 : (N == 128 && NB > 2) ? 2 
                 for (int s = 0; s < x.ccnt; ++s) {
                     float u, w;
                     sample_uw(x.clo + x.ck0 + s, cb, cs, sn, c, &u, &w);
-                    const float m = bilerp_band<P>(Fb, R0, u, w);
+                    const float m = bilerp_band<P, S::BIMG>(Fb, R0, u, w);
                     W[(x.ck0 + s) * WP + cb] = m;
                     ps += m;
                 }
@@ -651,7 +656,7 @@ __global__ void __launch_bounds__(4 * N, N == 64 ? 4 : (N == 128 && NB > 2) ? 2 
                     for (int s = 0; s < x.ccnt; ++s) {
                         float u, w;
                         sample_uw(x.clo + x.ck0 + s, cb, cs, sn, c, &u, &w);
-                        const float f = bilerp_band<P>(Fb, R0, u, w);
+                        const float f = bilerp_band<P, S::BIMG>(Fb, R0, u, w);
                         W[(x.ck0 + s) * WP + cb] = f;
                         const float y = Xc[s * NT + tid];
                         acc1 = fmaf(ex2(y), f, acc1);

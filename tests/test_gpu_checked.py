@@ -2,7 +2,8 @@
 -DBOAC_CHECKED).  It runs boac_mlem's small-batch path (the unfused grouped
 kernels), the fused one-CTA kernel and its cluster mode, and the score
 gradient (the fused gradient kernel and the batched reverse mode) on small
-cases through the C ABI: every checked shared-memory index and schedule
+cases through the C ABI, and the 256 x 256 band kernel: every checked
+shared-memory index and schedule
 entry is in range (fault count 0, summed over every translation unit), and
 the results equal the normal build's bit for bit (the checks change no
 arithmetic)."""
@@ -114,3 +115,38 @@ def test_checked_build_gradient(cuda):
             np.testing.assert_array_equal(Gc, Gr)
     assert chk.boac_bounds_faults(ctypes.byref(faults), 0) == _lib.BOAC_OK
     assert faults.value == 0
+
+
+def run_band(lib, p, dev, K, cfg=6):
+    """Images and scores of the band kernel (clusters of 5 CTAs at 256 x 256)
+    through the ragged entry point of `lib`."""
+    g = Geom.make(p.n, p.dx, p.V)
+    B = p.mu.shape[0]
+    mu = torch.tensor(p.mu, dtype=torch.float32, device=dev)
+    S = torch.tensor(p.S, dtype=torch.float32, device=dev)
+    batch = boac.RaggedBatch([g], [0] * B, [K] * B, list(mu), [S] * B, device=dev)
+    c = (ctypes.c_int * 1)(cfg)
+    nbytes = lib.boac_mlem_ragged_workspace_bytes(batch.geo, 1, batch.cands, B, c)
+    assert nbytes > 0
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    st = lib.boac_mlem_ragged(batch.geo, 1, batch.cands, B, _p(batch.mu_pool), _p(batch.S_pool),
+                              _p(batch.F_pool), _p(batch.L), 1, c, _p(ws), nbytes, _stream())
+    assert st == _lib.BOAC_OK, _lib.status_string(st)
+    torch.cuda.synchronize()
+    return batch.F_pool.view(B, p.n, p.n).cpu().numpy(), batch.L.cpu().numpy()
+
+
+def test_checked_build_band_kernel(cuda):
+    from paper_2109_11920_gb300 import build
+    build.build()
+    build.build(checked=True)
+    norm, chk = _lib.load(), _lib.load_checked()
+    faults = ctypes.c_int(-1)
+    assert chk.boac_bounds_faults(ctypes.byref(faults), 1) == _lib.BOAC_OK
+    p = make_problem(256, 0.1, 180, 1e6, B=2, seed=37)
+    Fr, Lr = run_band(norm, p, cuda, 2)
+    Fc, Lc = run_band(chk, p, cuda, 2)
+    assert chk.boac_bounds_faults(ctypes.byref(faults), 0) == _lib.BOAC_OK
+    assert faults.value == 0
+    np.testing.assert_array_equal(Fc, Fr)
+    np.testing.assert_array_equal(Lc, Lr)
