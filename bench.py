@@ -445,8 +445,9 @@ def run_gpu(args, rank, world, local_rank):
             "peak_kind": fp32_kind,
             "work_model": f"{FLOPS_PER_SAMPLE} FP32 ops per ray sample per view per iteration",
             "algorithmic_flops_per_launch": flops, "kernel_ms": 1e3 * kavg_s,
-            "timed": "CUDA events around boac_mlem on its stream: the scatter-schedule kernel, the two "
-                     "small kernels that sum the shared sinogram's ln S! term and the fused kernel"}
+            "timed": "CUDA events around boac_mlem on its stream: the scatter-schedule check (a build "
+                     "only on the geometry's first call) and tag kernels, the two small kernels that sum "
+                     "the shared sinogram's ln S! term and the fused kernel"}
     peak, peak_kind = measured_peak_gbs()
     alg = algorithmic_bytes_per_cand_iter(WL.n, WL.V) * cand_its
     # What-if: the same launch against HBM, counting the bytes the
