@@ -54,8 +54,12 @@ struct FusedShape {
     // multiple of 32 spreads rotated rows of samples over the banks.
     static constexpr int P = N + 1;
     static constexpr int IMG = (N + 1) * (N + 2) + 1;
+    static constexpr int IMGA = (IMG + 3) & ~3;  // an image's floats, rounded to 16 bytes
     static constexpr int NN = N * N;
-    static constexpr int WP = N + 1;         // sample-buffer pitch (odd)
+    // Sample-buffer pitch: rows start 16 bytes apart in whole groups, and a
+    // quarter-warp's 16-byte row accesses (threads on consecutive rows) fall
+    // on 8 different 16-byte bank groups since (N + 4) / 4 is odd.
+    static constexpr int WP = N + 4;
     static constexpr int NSEG = NT / N;      // segments per column / row
     static constexpr int SEG = N / NSEG;     // samples per segment
     static_assert(NT % N == 0 && N % NSEG == 0, "segmentation");
@@ -92,7 +96,7 @@ __host__ __device__ constexpr bool fused_global_images(int n) { return n > 128; 
 template <int N, int NT>
 __host__ __device__ constexpr size_t fused_image_floats() {
     using L = FusedShape<N, NT>;
-    return 2 * (size_t)L::IMG + (size_t)N * L::WP;
+    return 2 * (size_t)L::IMGA + (size_t)N * L::WP;
 }
 
 template <int N, int NT>
@@ -128,7 +132,7 @@ __device__ __forceinline__ const unsigned short* grid_sched(const FusedArgs& a, 
 template <int N, int NT, bool QUAD, int G = 1>
 __global__ void __launch_bounds__(NT, (G > 1 ? 1 : fused_min_blocks<N, NT>())) mlem_fused_kernel(FusedArgs a) {
     using Lay = FusedShape<N, NT>;
-    constexpr int P = Lay::P, IMG = Lay::IMG, NN = Lay::NN, WP = Lay::WP;
+    constexpr int P = Lay::P, IMG = Lay::IMG, IMGA = Lay::IMGA, NN = Lay::NN, WP = Lay::WP;
     constexpr int NSEG = Lay::NSEG, SEG = Lay::SEG;
     constexpr float kLog2e = 1.44269504088896340736f;
 
@@ -137,8 +141,8 @@ __global__ void __launch_bounds__(NT, (G > 1 ? 1 : fused_min_blocks<N, NT>())) m
                                 ? a.img + (size_t)blockIdx.x * fused_image_floats<N, NT>()
                                 : smem;
     float* img0 = img_base;             // F (mu during set-up), padded
-    float* img1 = img0 + IMG;           // back-projection accumulator, padded
-    float* W = img1 + IMG;              // [N][WP] grid samples / weights
+    float* img1 = img0 + IMGA;          // back-projection accumulator, padded
+    float* W = img1 + IMGA;             // [N][WP] grid samples / weights
     float* redc = fused_global_images(N) ? smem : W + N * WP;  // [2][NSEG][N] column partial sums
     float* redr = redc + 2 * NSEG * N;  // [2][NSEG][N] row partial sums
     float* rr = redr + 2 * NSEG * N;    // [4][N] ratios r = S / q per view
@@ -264,8 +268,14 @@ __global__ void __launch_bounds__(NT, (G > 1 ? 1 : fused_min_blocks<N, NT>())) m
             }
             if (QUAD) {  // rows: prefix sums from b = 0
                 float pr = 0.0f;
-#pragma unroll 8
-                for (int s = 0; s < SEG; ++s) pr += W[lb * WP + k0 + s];
+#pragma unroll 2
+                for (int s4 = 0; s4 < SEG; s4 += 4) {
+                    const float4 m4 = *reinterpret_cast<const float4*>(W + lb * WP + k0 + s4);
+                    pr += m4.x;
+                    pr += m4.y;
+                    pr += m4.z;
+                    pr += m4.w;
+                }
                 redr[seg * N + lb] = pr;
                 __syncthreads();
                 float before = 0.0f, total = 0.0f;
@@ -276,12 +286,15 @@ __global__ void __launch_bounds__(NT, (G > 1 ? 1 : fused_min_blocks<N, NT>())) m
                     if (s2 < seg) before += v;
                 }
                 float pre = before;
-#pragma unroll 8
-                for (int s = 0; s < SEG; ++s) {
-                    const int b = k0 + s;
-                    const float m = W[lb * WP + b];
-                    XrT[tab_ix(N, b, lb)] = ndl * (0.5f * m + pre);
-                    pre += m;
+#pragma unroll 2
+                for (int s4 = 0; s4 < SEG; s4 += 4) {
+                    const float4 m4 = *reinterpret_cast<const float4*>(W + lb * WP + k0 + s4);
+                    const float mm[4] = {m4.x, m4.y, m4.z, m4.w};
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        XrT[tab_ix(N, k0 + s4 + j, lb)] = ndl * (0.5f * mm[j] + pre);
+                        pre += mm[j];
+                    }
                 }
                 if (seg == 0) Ur[lb] = ndl * total;
             }
@@ -298,11 +311,16 @@ __global__ void __launch_bounds__(NT, (G > 1 ? 1 : fused_min_blocks<N, NT>())) m
             if (QUAD) {
                 __syncthreads();
                 const float ur = Ur[lb];
-#pragma unroll 8
-                for (int s = 0; s < SEG; ++s) {
-                    const int b = k0 + s;
-                    const float y = XrT[tab_ix(N, b, lb)];
-                    W[lb * WP + b] += dx * (ex2(y) + ex2(ur - y));
+#pragma unroll 2
+                for (int s4 = 0; s4 < SEG; s4 += 4) {
+                    float4* w4 = reinterpret_cast<float4*>(W + lb * WP + k0 + s4);
+                    const float4 y4 = *reinterpret_cast<const float4*>(XrT + tab_ix(N, k0 + s4, lb));
+                    float4 v = *w4;
+                    v.x += dx * (ex2(y4.x) + ex2(ur - y4.x));
+                    v.y += dx * (ex2(y4.y) + ex2(ur - y4.y));
+                    v.z += dx * (ex2(y4.z) + ex2(ur - y4.z));
+                    v.w += dx * (ex2(y4.w) + ex2(ur - y4.w));
+                    *w4 = v;
                 }
             }
             __syncthreads();
@@ -418,11 +436,12 @@ __global__ void __launch_bounds__(NT, (G > 1 ? 1 : fused_min_blocks<N, NT>())) m
                     for (int s4 = 0; s4 < SEG; s4 += 4) {
                         const float4 y4 = *reinterpret_cast<const float4*>(XrT + tab_ix(N, k0 + s4, lb));
                         const float yy[4] = {y4.x, y4.y, y4.z, y4.w};
+                        const float4 f4 = *reinterpret_cast<const float4*>(W + lb * WP + k0 + s4);
+                        const float ff[4] = {f4.x, f4.y, f4.z, f4.w};
 #pragma unroll
                         for (int j = 0; j < 4; ++j) {
-                            const float f = W[lb * WP + k0 + s4 + j];
-                            acc3 = fmaf(ex2(yy[j]), f, acc3);
-                            acc4 = fmaf(ex2(ur - yy[j]), f, acc4);
+                            acc3 = fmaf(ex2(yy[j]), ff[j], acc3);
+                            acc4 = fmaf(ex2(ur - yy[j]), ff[j], acc4);
                         }
                     }
                     redr[seg * N + lb] = acc3;
@@ -465,10 +484,13 @@ __global__ void __launch_bounds__(NT, (G > 1 ? 1 : fused_min_blocks<N, NT>())) m
                     const float r3 = dx * rr[2 * N + lb], r4 = dx * rr[3 * N + lb];
                     for (int s4 = 0; s4 < SEG; s4 += 4) {
                         const float4 y4 = *reinterpret_cast<const float4*>(XrT + tab_ix(N, k0 + s4, lb));
-                        const float yy[4] = {y4.x, y4.y, y4.z, y4.w};
-#pragma unroll
-                        for (int j = 0; j < 4; ++j)
-                            W[lb * WP + k0 + s4 + j] += fmaf(ex2(yy[j]), r3, ex2(ur - yy[j]) * r4);
+                        float4* w4 = reinterpret_cast<float4*>(W + lb * WP + k0 + s4);
+                        float4 v = *w4;
+                        v.x += fmaf(ex2(y4.x), r3, ex2(ur - y4.x) * r4);
+                        v.y += fmaf(ex2(y4.y), r3, ex2(ur - y4.y) * r4);
+                        v.z += fmaf(ex2(y4.z), r3, ex2(ur - y4.z) * r4);
+                        v.w += fmaf(ex2(y4.w), r3, ex2(ur - y4.w) * r4);
+                        *w4 = v;
                     }
                 }
                 __syncthreads();
@@ -642,7 +664,8 @@ static int split_launch_t(const FusedArgs& a, int clusters, cudaStream_t st) {
     if (s != BOAC_OK) return s;
     FusedArgs b = a;
     if (b.sched) {  // the scatter schedule of this geometry, then the kernel
-        b.sched = sched_prepare(N, b.V, b.V / 4, const_cast<unsigned short*>(a.sched), st, &s);
+        b.sched = sched_prepare(N, b.V, b.V / 4, FusedShape<N, NT>::WP, const_cast<unsigned short*>(a.sched), st,
+                                &s);
         if (s != BOAC_OK) return s;
     }
     cudaLaunchAttribute attr[1];
@@ -668,7 +691,8 @@ static int fused_launch_t(const FusedArgs& a, int slots, cudaStream_t st) {
     if constexpr (N <= 128) {
         if (b.sched) {  // the scatter schedule of this geometry, then the kernel
             int s = BOAC_OK;
-            b.sched = sched_prepare(N, b.V, QUAD ? b.V / 4 : b.V / 2, const_cast<unsigned short*>(a.sched), st, &s);
+            b.sched = sched_prepare(N, b.V, QUAD ? b.V / 4 : b.V / 2, FusedShape<N, NT>::WP,
+                                    const_cast<unsigned short*>(a.sched), st, &s);
             if (s != BOAC_OK) return s;
         }
     }

@@ -753,7 +753,8 @@ int grad_fused_launch(const boac_geom* g, const GradFusedArgs& args, int G, int 
     if (clusters < 1) return BOAC_EINVAL;
     GradFusedArgs a = args;
     int s = BOAC_OK;
-    a.sched = sched_prepare(g->n, g->n_views, g->n_views / 4, const_cast<unsigned short*>(args.sched), st, &s);
+    a.sched = sched_prepare(g->n, g->n_views, g->n_views / 4, g->n + 1 /* GradShape<N>::WP */,
+                            const_cast<unsigned short*>(args.sched), st, &s);
     if (s != BOAC_OK) return s;
 #define X(NV)                                                           \
     if (g->n == NV) {                                                   \

@@ -52,21 +52,23 @@ inline size_t sched_bytes(int n, int ngrid) {
     return align256(sizeof(unsigned short) * 9 * sched_entries(n) * (size_t)ngrid);
 }
 
-// Tag of a cached schedule: the geometry it was built for (never 0).
-__host__ __device__ constexpr unsigned long long sched_tag_value(int n, int V, int ngrid) {
-    return 0xB0AC5C0000000000ull ^ ((unsigned long long)n << 40) ^ ((unsigned long long)V << 20) ^
-           (unsigned long long)ngrid;
+// Tag of a cached schedule: the geometry and sample-buffer pitch it was
+// built for (never 0).
+__host__ __device__ constexpr unsigned long long sched_tag_value(int n, int V, int ngrid, int wp) {
+    return 0xB0AC5C0000000000ull ^ ((unsigned long long)n << 40) ^ ((unsigned long long)(wp - n) << 31) ^
+           ((unsigned long long)V << 20) ^ (unsigned long long)ngrid;
 }
 
-// One CTA per (grid, class).  With a tag that already holds `want` (a cached
-// schedule of this geometry) every CTA returns at once.
-template <int N>
+// One CTA per (grid, class), for a sample buffer of pitch WP (the W banks of
+// the rounds).  With a tag that already holds `want` (a cached schedule of
+// this geometry and pitch) every CTA returns at once.
+template <int N, int WP>
 __global__ void __launch_bounds__(256) scatter_schedule_kernel(int V, unsigned short* __restrict__ sched,
                                                                const unsigned long long* tag,
                                                                unsigned long long want) {
     using S = SchedShape<N>;
     if (tag != nullptr && *reinterpret_cast<const volatile unsigned long long*>(tag) == want) return;
-    constexpr int P = N + 1, WP = N + 1;
+    constexpr int P = N + 1;  // the padded accumulator's pitch
     const int gi = blockIdx.x / 9, cls = blockIdx.x % 9;
     const int pk = cls / 3, pb = cls % 3;
     const int nbc = (N - pb + 2) / 3, cnt = ((N - pk + 2) / 3) * nbc;
@@ -181,26 +183,35 @@ __global__ void __launch_bounds__(256) scatter_schedule_kernel(int V, unsigned s
         out[sched_slot(t / 32, t % 32)] = kSchedEmpty;
 }
 
-// Launch the schedule builder for a one-CTA configuration (images up to
-// 128 x 128): ngrid x 9 CTAs (skipped on the device when *tag == want).
-inline int sched_launch(int n, int V, int ngrid, unsigned short* sched, cudaStream_t st,
+// Launch the schedule builder for images up to 128 x 128 and a sample
+// buffer of pitch wp (n + 1 or n + 4): ngrid x 9 CTAs (skipped on the
+// device when *tag == want).
+inline int sched_launch(int n, int V, int ngrid, int wp, unsigned short* sched, cudaStream_t st,
                         const unsigned long long* tag = nullptr, unsigned long long want = 0) {
+#define BOAC_SCHED_CASE(NV)                                                                              \
+    case NV:                                                                                             \
+        if (wp == NV + 4) scatter_schedule_kernel<NV, NV + 4><<<ngrid * 9, 256, 0, st>>>(V, sched, tag, want); \
+        else if (wp == NV + 1) scatter_schedule_kernel<NV, NV + 1><<<ngrid * 9, 256, 0, st>>>(V, sched, tag, want); \
+        else return BOAC_EINVAL;                                                                         \
+        break;
     switch (n) {
-        case 64: scatter_schedule_kernel<64><<<ngrid * 9, 256, 0, st>>>(V, sched, tag, want); break;
-        case 96: scatter_schedule_kernel<96><<<ngrid * 9, 256, 0, st>>>(V, sched, tag, want); break;
-        case 128: scatter_schedule_kernel<128><<<ngrid * 9, 256, 0, st>>>(V, sched, tag, want); break;
+        BOAC_SCHED_CASE(64)
+        BOAC_SCHED_CASE(96)
+        BOAC_SCHED_CASE(128)
         default: return BOAC_OK;
     }
+#undef BOAC_SCHED_CASE
     return launch_status();
 }
 
-// The schedule of geometry (n, V, ngrid) for a launch on stream st: a slot
-// of the device-side cache (built there when its tag does not name the
-// geometry), or, when no slot is free or the schedule is larger than a
-// slot, built into ws (sched_bytes(n, ngrid) bytes of the caller's
-// workspace).  Returns the schedule's address; *status is BOAC_OK or the
-// launch error.
-const unsigned short* sched_prepare(int n, int V, int ngrid, unsigned short* ws, cudaStream_t st, int* status);
+// The schedule of geometry (n, V, ngrid) and sample-buffer pitch wp for a
+// launch on stream st: a slot of the device-side cache (built there when its
+// tag does not name the geometry and pitch), or, when no slot is free or the
+// schedule is larger than a slot, built into ws (sched_bytes(n, ngrid) bytes
+// of the caller's workspace).  Returns the schedule's address; *status is
+// BOAC_OK or the launch error.
+const unsigned short* sched_prepare(int n, int V, int ngrid, int wp, unsigned short* ws, cudaStream_t st,
+                                    int* status);
 
 // A thread's words of one class of a grid's schedule (word t = tid + i NT:
 // warp w's lanes hold rounds 2 (w + i NT / 32) and that + 1).

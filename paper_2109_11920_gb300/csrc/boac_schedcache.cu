@@ -1,8 +1,9 @@
 // boac_schedcache.cu -- the scatter schedules of the geometries in use, kept
 // on the device across calls.
 //
-// A schedule (boac_sched.cuh) depends on the image size, the view count and
-// the number of sample grids only; building one takes about 0.27 ms at
+// A schedule (boac_sched.cuh) depends on the image size, the view count,
+// the number of sample grids and the pitch of the kernel's sample buffer
+// only; building one takes about 0.27 ms at
 // 128 x 128 / 120 views, a tenth of a 16-candidate call.  The library keeps
 // kSchedCacheSlots schedules in static device memory, each slot with a
 // device-side tag naming the geometry it holds.  Static device memory is
@@ -32,7 +33,7 @@ constexpr size_t kSchedCacheEntries = ((size_t)4 << 20) / sizeof(unsigned short)
 constexpr int kSchedCacheDevices = 64;
 
 struct SlotGeom {
-    int n, V, ngrid;  // n == 0: free
+    int n, V, ngrid, wp;  // n == 0: free
 };
 
 std::mutex g_sched_mu;
@@ -45,26 +46,27 @@ static __device__ unsigned long long g_sched_tag[kSchedCacheSlots];
 
 __global__ void sched_tag_kernel(unsigned long long* tag, unsigned long long v) { *tag = v; }
 
-// The slot of (n, V, ngrid) on device dev, assigning a free one; -1 if none.
-static int sched_slot_of(int dev, int n, int V, int ngrid) {
+// The slot of (n, V, ngrid, wp) on device dev, assigning a free one; -1 if none.
+static int sched_slot_of(int dev, int n, int V, int ngrid, int wp) {
     std::lock_guard<std::mutex> lock(g_sched_mu);
     // slots are filled in order and never freed, so no match follows a free slot
     for (int i = 0; i < kSchedCacheSlots; ++i) {
         SlotGeom& s = g_sched_geom[dev][i];
-        if (s.n == n && s.V == V && s.ngrid == ngrid) return i;
+        if (s.n == n && s.V == V && s.ngrid == ngrid && s.wp == wp) return i;
         if (s.n == 0) {
-            s = SlotGeom{n, V, ngrid};
+            s = SlotGeom{n, V, ngrid, wp};
             return i;
         }
     }
     return -1;
 }
 
-const unsigned short* sched_prepare(int n, int V, int ngrid, unsigned short* ws, cudaStream_t st, int* status) {
+const unsigned short* sched_prepare(int n, int V, int ngrid, int wp, unsigned short* ws, cudaStream_t st,
+                                    int* status) {
     int dev = -1, slot = -1;
     if (sched_bytes(n, ngrid) <= sizeof(unsigned short) * kSchedCacheEntries && cudaGetDevice(&dev) == cudaSuccess &&
         dev >= 0 && dev < kSchedCacheDevices)
-        slot = sched_slot_of(dev, n, V, ngrid);
+        slot = sched_slot_of(dev, n, V, ngrid, wp);
     void* base = nullptr;
     void* tags = nullptr;
     if (slot >= 0 && (cudaGetSymbolAddress(&base, g_sched_cache) != cudaSuccess ||
@@ -73,13 +75,13 @@ const unsigned short* sched_prepare(int n, int V, int ngrid, unsigned short* ws,
         slot = -1;
     }
     if (slot < 0) {
-        *status = sched_launch(n, V, ngrid, ws, st);
+        *status = sched_launch(n, V, ngrid, wp, ws, st);
         return ws;
     }
     unsigned short* sched = static_cast<unsigned short*>(base) + (size_t)slot * kSchedCacheEntries;
     unsigned long long* tag = static_cast<unsigned long long*>(tags) + slot;
-    const unsigned long long want = sched_tag_value(n, V, ngrid);
-    *status = sched_launch(n, V, ngrid, sched, st, tag, want);
+    const unsigned long long want = sched_tag_value(n, V, ngrid, wp);
+    *status = sched_launch(n, V, ngrid, wp, sched, st, tag, want);
     if (*status != BOAC_OK) return sched;
     sched_tag_kernel<<<1, 1, 0, st>>>(tag, want);
     *status = launch_status();
